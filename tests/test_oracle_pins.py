@@ -1,0 +1,300 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test ties one oracle routine to a value the paper prints, a textbook
+value, a closed form, a library routine, an invariant, or a brute-force
+loop on tiny inputs, so that a dropped term, a wrong sign, a wrong index or a
+transposed operand in the oracle fails at least one of them.
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import synth
+from synth import configs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# ----------------------------------------------------------------- rounding
+
+def test_round_half_up_ties(orc):
+    # Eq. 4 leaves ties open; the reading is half-up.  Banker's rounding or
+    # truncation would fail here.
+    assert orc.round_half_up(0.5) == 1.0
+    assert orc.round_half_up(1.5) == 2.0
+    assert orc.round_half_up(2.5) == 3.0
+    assert orc.round_half_up(2.4999999) == 2.0
+    assert orc.round_half_up(7.0) == 7.0
+
+
+# ------------------------------------------------------------ trial DM list
+
+@pytest.mark.parametrize("df", [-0.39062, -0.390625])
+def test_dm_list_count_matches_paper(orc, df):
+    g = _golden("paper_values.json")["htru_benchmark"]
+    w = _golden("paper_values.json")["intrinsic_pulse_width_us"]["value"]
+    dms = orc.dm_list(g["nchans"], g["f0_mhz"], df, g["dt_s"], g["dm_lo"], g["dm_hi"],
+                      width_us=w, tol=1.25)
+    assert dms.size == g["ndm"]          # 1196 trials, Sec. 5.2
+    assert dms[0] == 0.0
+    assert np.all(np.diff(dms) > 0)
+    assert dms[-1] < g["dm_hi"]
+    steps = np.diff(dms)
+    # "approximately exponential spacing": steps grow with DM, roughly in
+    # proportion to DM at the top of the range
+    assert steps[-1] > 10 * steps[0]
+    hi = dms[:-1] > 200
+    ratio = steps[hi] / dms[:-1][hi]
+    assert ratio.max() / ratio.min() < 1.2
+
+
+# -------------------------------------------------------------- delay table
+
+def test_partial_delay_physical_scale(orc):
+    # Two channels at 2 GHz and 1 GHz, 1 us sampling, DM = 1: the textbook
+    # approximation gives 4.15 ms x (1 - 1/4) = 3.1125 ms = 3112.5 samples.
+    tb = _golden("textbook_values.json")["dispersion_ms_per_unit_dm_ghz2"]
+    expect = tb["value"] * 1e-3 * (1.0 / 1.0**2 - 1.0 / 2.0**2) / 1e-6
+    got = orc.partial_delay(2000.0, -1000.0, 1e-6, 1)
+    assert abs(got - expect) / expect < tb["rel_tol"]
+    tab = orc.delay_table(2, 2000.0, -1000.0, 1e-6, [1.0])
+    assert tab[0, 0] == 0 and abs(tab[0, 1] - expect) <= 0.5 + tb["rel_tol"] * expect
+
+
+def test_delay_table_invariants(orc):
+    c = configs.SURVEY
+    dms = orc.dm_list(c["nchans"], c["f0"], c["df"], c["dt"], 0.0, 1000.0)
+    tab = orc.delay_table(c["nchans"], c["f0"], c["df"], c["dt"], dms)
+    assert tab.shape == (1196, 1024)
+    assert np.all(tab[:, 0] == 0)            # nu = 0 is the reference channel
+    assert np.all(tab[0, :] == 0)            # DM = 0
+    assert np.all(np.diff(tab, axis=1) >= 0)  # descending band: later = lower freq
+    assert np.all(np.diff(tab, axis=0) >= 0)  # non-decreasing DM list
+    # Eq. 1 is linear in DM: doubling the DM doubles the delay (+-1 from rounding)
+    t1 = orc.delay_table(c["nchans"], c["f0"], c["df"], c["dt"], [100.0, 200.0])
+    assert np.max(np.abs(t1[1].astype(np.int64) - 2 * t1[0])) <= 1
+
+
+def test_delay_table_matches_exact_rational(orc):
+    # Evaluate Eq. 3-4 in exact rational arithmetic from the same double inputs
+    # and compare; only points within 1e-9 of a .5 tie may legitimately differ.
+    c = configs.SURVEY
+    dms = orc.dm_list(c["nchans"], c["f0"], c["df"], c["dt"], 0.0, 1000.0)
+    tab = orc.delay_table(c["nchans"], c["f0"], c["df"], c["dt"], dms)
+    rng = np.random.default_rng(7)
+    k = Fraction(4148808, 1000)
+    f0 = Fraction(c["f0"])
+    df = Fraction(c["df"])
+    dt = Fraction(c["dt"])
+    checked = 0
+    for d, ch in zip(rng.integers(0, dms.size, 400), rng.integers(0, 1024, 400)):
+        f = f0 + ch * df
+        x = Fraction(dms[d]) * (k / dt) * (1 / (f * f) - 1 / (f0 * f0))
+        frac = x - (x.numerator // x.denominator)
+        if abs(frac - Fraction(1, 2)) < Fraction(1, 10**9):
+            continue
+        exact = int((x + Fraction(1, 2)).numerator // (x + Fraction(1, 2)).denominator)
+        assert tab[d, ch] == exact
+        checked += 1
+    assert checked > 390
+
+
+def test_delay_table_rejects_bad_bands(orc):
+    with pytest.raises(ValueError):
+        orc.delay_table(16, 100.0, -10.0, 64e-6, [1.0])   # last channel at -50 MHz
+    with pytest.raises(ValueError):
+        orc.delay_table(16, 1400.0, +1.0, 64e-6, [1.0])   # ascending: negative delays
+
+
+# ----------------------------------------------------------- direct, Eq. 2
+
+def _brute_direct(samples, delays, nsamps, mask=None):
+    """Pure-Python loops over (d, t, c) on tiny inputs."""
+    ndm, nchans = delays.shape
+    out = np.zeros((ndm, nsamps), dtype=np.int64)
+    for d in range(ndm):
+        for t in range(nsamps):
+            s = 0
+            for ch in range(nchans):
+                m = 1 if mask is None else int(mask[ch])
+                s += m * int(samples[t + int(delays[d, ch]), ch])
+            out[d, t] = s
+    return out
+
+
+@pytest.mark.parametrize("nbits", [1, 2, 4, 8])
+def test_direct_matches_brute_force(orc, nbits):
+    nchans, nsamps = 12, 37
+    dms = [0.0, 3.0, 7.5, 20.0, 41.0]
+    delays = orc.delay_table(nchans, 400.0, -2.0, 1e-3, dms)
+    rows = nsamps + int(delays.max())
+    s = synth.uniform_samples(11, nbits, rows, nchans, nbits)
+    mask = np.ones(nchans, np.uint8)
+    mask[5] = 0
+    got = orc.direct(synth.pack(s, nbits), nbits, nchans, nsamps, delays, mask)
+    assert np.array_equal(got, _brute_direct(s, delays, nsamps, mask))
+
+
+def test_direct_dm0_is_channel_sum(orc):
+    c = configs.TINY
+    delays = orc.delay_table(c["nchans"], c["f0"], c["df"], c["dt"],
+                             configs.linear_dms(c["dms"]))
+    rows = 2048 + int(delays.max())
+    s = synth.normal_u8(1, 0, rows, c["nchans"])
+    got = orc.direct(s, 8, c["nchans"], 2048, delays[:1])
+    assert np.array_equal(got[0], np.sum(s[:2048].astype(np.int64), axis=1))
+
+
+def test_direct_recovers_injected_pulse(orc):
+    c = configs.TINY
+    dms = configs.linear_dms(c["dms"])
+    delays = orc.delay_table(c["nchans"], c["f0"], c["df"], c["dt"], dms)
+    rows = c["nsamps"] + int(delays.max())
+    noise = synth.normal_u8(c["seed"], 0, rows, c["nchans"])
+    p = c["pulses"][0]
+    sig = synth.inject_boxcar(noise, delays[p["dm_index"]], p["t0"], p["width"],
+                              amp=p["amp"])
+    d_sig = orc.direct(sig, 8, c["nchans"], c["nsamps"], delays).astype(np.int64)
+    d_noise = orc.direct(noise, 8, c["nchans"], c["nsamps"], delays).astype(np.int64)
+    # At this DM spacing the delay of the lowest channel moves by 3 samples per
+    # trial, less than the 4-sample boxcar, so trials 49..51 all collect the
+    # full pulse; noise decides between them.  The peak must be one of them.
+    d, t = np.unravel_index(np.argmax(d_sig), d_sig.shape)
+    assert abs(int(d) - p["dm_index"]) <= 1 and abs(int(t) - p["t0"]) <= p["width"]
+    # no clipping happened in the boxcar, so the excess is exactly 64 x 40
+    rowsel = p["t0"] + delays[p["dm_index"]][None, :] + np.arange(p["width"])[:, None]
+    assert noise[rowsel, np.arange(c["nchans"])[None, :]].max() <= 255 - p["amp"]
+    ex = d_sig[p["dm_index"], p["t0"]:p["t0"] + p["width"]] - \
+        d_noise[p["dm_index"], p["t0"]:p["t0"] + p["width"]]
+    assert np.all(ex == c["nchans"] * p["amp"])
+    # the full excess is reached only within one trial of the true DM
+    excess_all = (d_sig - d_noise).max(axis=1)
+    full = np.flatnonzero(excess_all == c["nchans"] * p["amp"])
+    assert p["dm_index"] in full and full.min() >= p["dm_index"] - 1 \
+        and full.max() <= p["dm_index"] + 1
+
+
+def test_direct_is_linear_and_mask_removes_one_channel(orc):
+    nchans, nsamps = 32, 500
+    delays = orc.delay_table(nchans, 1400.0, -4.0, 64e-6, np.linspace(0, 300, 9))
+    rows = nsamps + int(delays.max())
+    a = synth.uniform_samples(3, 1, rows, nchans, 7)
+    b = synth.uniform_samples(3, 2, rows, nchans, 7)
+    da = orc.direct(a, 8, nchans, nsamps, delays).astype(np.int64)
+    db = orc.direct(b, 8, nchans, nsamps, delays).astype(np.int64)
+    dab = orc.direct((a + b).astype(np.uint8), 8, nchans, nsamps, delays).astype(np.int64)
+    assert np.array_equal(dab, da + db)
+    mask = np.ones(nchans, np.uint8)
+    mask[17] = 0
+    dk = orc.direct(a, 8, nchans, nsamps, delays, mask).astype(np.int64)
+    t = np.arange(nsamps)
+    for d in range(delays.shape[0]):
+        assert np.array_equal(da[d] - dk[d], a[t + delays[d, 17], 17])
+
+
+@pytest.mark.parametrize("nbits", [1, 2, 4])
+def test_packed_formats_equal_unpacked(orc, nbits):
+    nchans, nsamps = 40, 300
+    delays = orc.delay_table(nchans, 1500.0, -3.0, 64e-6, np.linspace(0, 200, 6))
+    rows = nsamps + int(delays.max())
+    s = synth.uniform_samples(5, nbits, rows, nchans, nbits)
+    assert np.array_equal(synth.unpack(synth.pack(s, nbits), nbits, nchans), s)
+    assert np.array_equal(orc.direct(synth.pack(s, nbits), nbits, nchans, nsamps, delays),
+                          orc.direct(s, 8, nchans, nsamps, delays))
+
+
+def test_direct_f32_matches_numpy_gather(orc):
+    nchans, nsamps = 48, 700
+    delays = orc.delay_table(nchans, 1500.0, -3.0, 64e-6, np.linspace(0, 250, 7))
+    rows = nsamps + int(delays.max())
+    x = synth.normal_f32(9, 0, rows, nchans)
+    got, ab = orc.direct_f32(x, nsamps, delays)
+    t = np.arange(nsamps)[:, None]
+    for d in range(delays.shape[0]):
+        g = x[t + delays[d][None, :], np.arange(nchans)[None, :]].astype(np.float64)
+        assert np.allclose(got[d], g.sum(axis=1), rtol=0, atol=1e-9)
+        assert np.allclose(ab[d], np.abs(g).sum(axis=1), rtol=0, atol=1e-9)
+
+
+def test_direct_points_agree_with_full(orc):
+    nchans, nsamps = 24, 400
+    delays = orc.delay_table(nchans, 1500.0, -5.0, 64e-6, np.linspace(0, 150, 5))
+    rows = nsamps + int(delays.max())
+    s = synth.uniform_samples(2, 0, rows, nchans, 2)
+    full = orc.direct(synth.pack(s, 2), 2, nchans, nsamps, delays)
+    rng = np.random.default_rng(1)
+    ds = rng.integers(0, 5, 50)
+    ts = rng.integers(0, nsamps, 50)
+    pts = orc.direct_points(synth.pack(s, 2), 2, nchans, delays, ds, ts)
+    assert np.array_equal(pts, full[ds, ts])
+
+
+# ----------------------------------------------------------------- sub-band
+
+def _sb_case(orc, nchans=64, nsamps=600, nbits=2, ndm=20):
+    dms = np.linspace(0.0, 500.0, ndm)
+    delays = orc.delay_table(nchans, 1500.0, -2.0, 64e-6, dms)
+    rows = nsamps + int(delays.max()) + 64
+    s = synth.uniform_samples(4, 0, rows, nchans, nbits)
+    return delays, synth.pack(s, nbits), s
+
+
+def test_subband_one_trial_per_group_is_direct(orc):
+    delays, packed, _ = _sb_case(orc)
+    direct = orc.direct(packed, 2, 64, 600, delays)
+    assert np.array_equal(orc.subband(packed, 2, 64, 8, 1, delays, 600), direct)
+
+
+def test_subband_one_channel_per_subband_is_direct(orc):
+    delays, packed, _ = _sb_case(orc)
+    direct = orc.direct(packed, 2, 64, 600, delays)
+    assert np.array_equal(orc.subband(packed, 2, 64, 1, 4, delays, 600), direct)
+
+
+def test_subband_single_subband_is_direct_at_nominal(orc):
+    delays, packed, _ = _sb_case(orc)
+    direct = orc.direct(packed, 2, 64, 600, delays)
+    got = orc.subband(packed, 2, 64, 64, 4, delays, 600)
+    for d in range(delays.shape[0]):
+        assert np.array_equal(got[d], direct[(d // 4) * 4])
+
+
+def test_subband_nominal_trials_are_exact(orc):
+    delays, packed, _ = _sb_case(orc)
+    direct = orc.direct(packed, 2, 64, 600, delays)
+    got = orc.subband(packed, 2, 64, 16, 5, delays, 600)
+    for g in range(0, delays.shape[0], 5):
+        assert np.array_equal(got[g], direct[g])
+    assert not np.array_equal(got, direct)   # the other trials are approximate
+
+
+def test_subband_max_delay_bounds_reads(orc):
+    delays, _, _ = _sb_case(orc)
+    m = orc.subband_max_delay(delays, 16, 5)
+    direct_m = int(delays.max())
+    # nominal DM <= trial DM inside each sub-band, so reads never pass the
+    # direct maximum by more than the +1 of rounded differences, and they
+    # reach at least the stage-2 shift of the last sub-band
+    assert int(delays[:, 48].max()) <= m <= direct_m + 1
+    assert orc.subband_max_delay(delays, 16, 1) == direct_m
+
+
+def test_subband_smear_bound_matches_taylor_form(orc):
+    # App. B: the exact bound and its first-order Taylor form agree to O(r^2).
+    f0, df, n = 1581.8, -0.390625, 1024
+    for nsub in (4, 8, 16):
+        ex = orc.subband_smear_bound(f0, df, 64e-6, n, nsub, 10.0)
+        ty = orc.subband_smear_taylor(f0, df, n, nsub, 10.0)
+        r = nsub / n
+        assert ex > 0 and ty > 0
+        assert abs(ex - ty) / ex < 10 * r
+    assert orc.relative_smearing(1.0, 0.0) == 1.0
+    assert abs(orc.relative_smearing(3.0, 4.0) - 5.0 / 3.0) < 1e-15
