@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark of the direct dedispersion hot path on the survey-shaped workload.
+
+Workload (the paper's HTRU-like benchmark of Sec. 5.2, synthetic data of the
+same shape): 1024 channels of 2-bit samples from 1581.8 MHz down in steps of
+0.390625 MHz, dt = 64 us, 1196 trial DMs over 0 <= DM < 1000 from the
+bounded-smearing rule, gulps of 2^19 output samples.  One step = one gulp
+through ``dd_execute`` (unpack/corner turn + dedispersion kernel) with the
+input already resident in HBM.  Inputs (139 MB) and outputs (2.5 GB) are both
+larger than the 129 MB L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+this workload instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+from synth import configs  # noqa: E402
+
+METRIC = "direct dedisp Gchan·DM·samp/s, % roofline, real-time factor; stream p99 latency"
+UNIT = "Gchan*DM*samp/s"
+WORKLOAD = "survey-1024ch-u2: 1024 ch 2-bit, 1196 trials DM 0-1000, 2^19 samples/gulp"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _make_input(plan_dms, delays, G, max_delay):
+    c = configs.SURVEY
+    rows = G + max_delay
+    x = synth.uniform_packed(c["seed"], 0, rows, c["nchans"], 2)
+    for p in c["pulses"]:
+        k = int(np.argmin(np.abs(plan_dms - p["dm"])))
+        x = synth.inject_boxcar_packed(x, 2, c["nchans"], delays[k], p["t0"], p["width"],
+                                       p["value"])
+    return x
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="ddclk", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ cpu oracle
+
+def cpu_oracle_rate(x, delays, G, seconds):
+    """Time the CPU oracle (as it stands) on a bounded sample of the workload:
+    trials evenly spaced over the list, all channels, a prefix of the gulp.
+    Returns (Gchan*DM*samp/s, cores, description)."""
+    import oracle
+    oracle.build()
+    nchans = delays.shape[1]
+    probe_d = np.linspace(0, delays.shape[0] - 1, 8).astype(int)
+    t0 = time.perf_counter()
+    oracle.direct(x, 2, nchans, 2048, delays[probe_d])
+    dt = max(time.perf_counter() - t0, 1e-3)
+    rate = 8 * 2048 * nchans / dt
+    want = rate * seconds
+    ntr = int(min(delays.shape[0], max(8, want // (nchans * 16384))))
+    ns = int(min(G, max(2048, want // (nchans * ntr))))
+    sel = np.linspace(0, delays.shape[0] - 1, ntr).astype(int)
+    t0 = time.perf_counter()
+    oracle.direct(x, 2, nchans, ns, delays[sel])
+    dt = time.perf_counter() - t0
+    adds = float(ntr) * ns * nchans
+    desc = "%d of %d trials (evenly spaced) x %d of %d samples x %d channels" % (
+        ntr, delays.shape[0], ns, G, nchans)
+    return adds / dt / 1e9, oracle.num_threads(), desc, dt
+
+
+# --------------------------------------------------------------- reference
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    c = configs.SURVEY
+    dms = oracle.dm_list(c["nchans"], c["f0"], c["df"], c["dt"], 0.0, 1000.0)
+    delays = oracle.delay_table(c["nchans"], c["f0"], c["df"], c["dt"], dms)
+    G = c["nsamps"]
+    x = _make_input(dms, delays, G, int(delays.max()))
+    nchans = c["nchans"]
+    # each step: a bounded sample of the workload (evenly spaced trials, a
+    # prefix of the gulp) sized to a few seconds of CPU work
+    ntr, ns = 24, 16384
+    sel = np.linspace(0, delays.shape[0] - 1, ntr).astype(int)
+    sub = delays[sel]
+    for _ in range(a.warmup):
+        oracle.direct(x, 2, nchans, ns, sub)
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        oracle.direct(x, 2, nchans, ns, sub)
+        times.append(time.perf_counter() - t0)
+    T = sum(times)
+    value = a.steps * ntr * ns * nchans / T / 1e9
+    desc = "%d of %d trials (evenly spaced) x %d of %d samples x %d channels per step" % (
+        ntr, delays.shape[0], ns, G, nchans)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * T / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "nchans": nchans,
+                                        "ndm": int(delays.shape[0]), "gulp": G, "nbits": 2},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# -------------------------------------------------------------------- ours
+
+def run_ours(a, rank, world, local_rank):
+    import torch
+    import paper_1201_5380_gb300 as dd
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    c = configs.SURVEY
+    nchans, G = c["nchans"], c["nsamps"]
+    plan = dd.Plan(nchans, c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0),
+                   gulp=G)
+    ndm = plan.dm_count
+    delays = plan.delay_table()
+    x = _make_input(plan.dms, delays, G, plan.max_delay)
+    in_bytes = x.nbytes
+    out_bytes = ndm * G * 4
+    d_in = torch.from_numpy(x).to(dev)
+    out = torch.empty((ndm, G), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(a.warmup):
+        plan.execute(d_in, 2, G, out, stream=stream)
+    torch.cuda.synchronize(dev)
+    if plan.device_status() != 0:
+        raise RuntimeError("device-side bound flag set during warm-up")
+    peak_adds, _ = dd.probe_int_add(1 << 16, stream=stream)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clk = ClockSampler(local_rank)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    plan.reset_kernel_timing()
+    plan.set_kernel_timing(True)
+    clk.start()
+    time.sleep(0.3)
+    evs[0].record(stream)
+    for i in range(a.steps):
+        plan.execute(d_in, 2, G, out, stream=stream)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = clk.stop()
+    barrier()
+    plan.set_kernel_timing(False)
+    dd_ms, dd_n = plan.kernel_timing(1)
+    ct_ms, ct_n = plan.kernel_timing(0)
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / a.steps
+    units = float(nchans) * ndm * G
+    value = world * units * a.steps / (total_ms / 1e3) / 1e9
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    h_in = torch.empty(x.shape, dtype=torch.uint8, pin_memory=True)
+    h_in.numpy()[:] = x
+    h_out = torch.empty((ndm, G), dtype=torch.int32, pin_memory=True)
+    hin, hout = h_in.numpy(), h_out.numpy()
+    plan.execute(hin, 2, G, hout)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.e2e_steps):
+        plan.execute(hin, 2, G, hout)
+    e2e_s = (time.perf_counter() - t0) / a.e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * units / e2e_s / 1e9
+    if not np.array_equal(hout.view(np.uint32)[:, :64],
+                          out[:, :64].cpu().numpy().view(np.uint32)):
+        raise RuntimeError("host-path output differs from device-path output")
+
+    # roofline of the dedispersion kernel: algorithmic adds per launch over its
+    # measured duration, against the measured integer-add rate
+    k_ms = dd_ms / max(dd_n, 1)
+    achieved = units / (k_ms / 1e3)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    byte_floor_ms = (in_bytes + out_bytes) / (hbm * 1e9) * 1e3
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nchans": nchans, "ndm": ndm, "gulp": G, "nbits": 2,
+                   "max_delay": plan.max_delay, "tuning": plan.get_tuning(),
+                   "l2": "inputs larger than L2 (139 MB in, 2.5 GB out per step); no flush",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "rtf": G * c["dt"] / (ms_step / 1e3),
+        "step_ms_p5_p50_p95": [float(np.percentile(step_ms, q)) for q in (5, 50, 95)],
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(in_bytes),
+                "d2h_bytes_per_step": int(out_bytes), "ms_per_step": e2e_s * 1e3},
+        "gpu_launches": int(dd_n + ct_n),
+        "kernels_ms_per_step": {"dedisp": k_ms, "corner_turn": ct_ms / max(ct_n, 1)},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12,
+                     "unit": "Tadd/s", "frac": achieved / peak_adds, "traffic": None,
+                     "peak_source": "measured integer-add probe (dd_probe_int_add)",
+                     "byte_floor_ms": byte_floor_ms, "compute_floor_ms": units / peak_adds * 1e3,
+                     "hbm_gbs_used": hbm},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        oracle_delays = oracle.delay_table(nchans, c["f0"], c["df"], c["dt"], plan.dms)
+        v, cores, desc, secs = cpu_oracle_rate(x, oracle_delays, G, a.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": desc, "seconds": secs}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def main():
+    a = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return run_reference(a, rank, world)
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        return run_ours(a, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,244 @@
+/*
+ * dedisp.h - C ABI of a GB300 (sm_103a) library for incoherent
+ * dedispersion, after Barsdell, Bailes, Barnes & Fluke, "Accelerating
+ * incoherent dedispersion" (arXiv:1201.5380).
+ *
+ * What it computes
+ *   Direct transform, Sec. 2.1 Eq. 2:
+ *       D[d][t] = sum_{c < N_nu} mask[c] * A[c][t + delay(d, c)],
+ *   with the per-channel delay of Eq. 3-4:
+ *       Delta T(c)   = (k_DM / dtau) * ((nu0 + c*dnu)^-2 - nu0^-2),
+ *       delay(d, c)  = round(DM(d) * Delta T(c)),   k_DM = 4.148808e3,
+ *   where round() is round-half-up (floor(x + 0.5)) evaluated in IEEE double
+ *   on the host, and the kill mask is applied arithmetically (Sec. 2.3).
+ *   Sub-band variant, Sec. 4.1 with Eq. (eq:combining_subbands):
+ *       S[g][n][t] = sum_{c' < N'} A[nN'+c'][t + delay(gn, nN'+c') - delay(gn, nN')]
+ *       D[d][t]    = sum_{n < N_SB} S[g(d)][n][t + delay(d, nN')]
+ *   with trials grouped consecutively N'_DM per group and gn the group's
+ *   first (lowest) trial, the early-edge alignment of Appendix B.
+ *
+ * Data layouts
+ *   Input: a time-major filterbank.  Row t (t = 0 .. nsamps_out + max_delay
+ *   - 1) starts at byte t * in_row_stride_bytes and holds channels
+ *   0 .. nchans-1.  For in_nbits = 1, 2 or 4, channel c occupies bits
+ *   [(c*nbits) mod 8, +nbits) of byte (c*nbits)/8 of the row, least
+ *   significant bits first; in_nbits = 8 is one unsigned byte per channel;
+ *   in_nbits = DD_IN_F32 is one little-endian float per channel.
+ *   Channel 0 is at frequency nu0 (f0_mhz); channel c at f0_mhz + c*df_mhz.
+ *   Output: DM-major, row d (one per trial) of nsamps_out samples starting
+ *   at element d * out_row_stride_elems.  Integer input gives uint32 sums
+ *   (exact); float input gives float sums (FP32 accumulation).
+ *
+ * Ownership and threading
+ *   Handles are created and destroyed by the library.  Input and output
+ *   buffers always belong to the caller; the library never keeps a caller
+ *   pointer after a call returns.  A plan binds to the CUDA device that is
+ *   current when it is created and must be used with that device current.
+ *   A plan, stream or batch handle may be used by one host thread at a time.
+ *
+ * Errors
+ *   Every call returns a dd_status; nothing is thrown across the ABI.  On
+ *   an error the output buffer's contents are unspecified (its size is never
+ *   exceeded).  Device-side bound checks never trap: they record a flag that
+ *   dd_plan_get_device_status returns.
+ */
+#ifndef GB300_DEDISP_H
+#define GB300_DEDISP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DD_ABI_VERSION 1
+
+typedef enum dd_status {
+    DD_OK = 0,
+    DD_ERR_INVALID_ARG = 1,       /* null handle/pointer, bad size, bad band */
+    DD_ERR_NO_DM_LIST = 2,        /* execute before a DM list was set */
+    DD_ERR_UNSUPPORTED_NBITS = 3, /* in_nbits not in {1, 2, 4, 8, 32} */
+    DD_ERR_INPUT_TOO_SHORT = 4,   /* fewer than nsamps_out + max_delay rows */
+    DD_ERR_OOM = 5,               /* device or host allocation failed */
+    DD_ERR_CUDA = 6,              /* a CUDA runtime call failed */
+    DD_ERR_TIMEOUT = 7,           /* a bounded wait expired */
+    DD_ERR_DEVICE_BOUNDS = 8,     /* a kernel clamped an out-of-range index */
+    DD_ERR_OVERFLOW = 9,          /* nchans * max sample could exceed uint32 */
+    DD_ERR_NOT_READY = 10,        /* request not finished yet */
+    DD_ERR_REJECTED = 11          /* admission control refused the request */
+} dd_status;
+
+/* in_nbits value for 32-bit float samples */
+#define DD_IN_F32 32
+
+/* dd_execute / dd_stream_push flags */
+#define DD_DEVICE_PTRS 0x1u /* in and out are device pointers; the call is
+                               asynchronous on cuda_stream.  Otherwise they
+                               are host pointers and the call copies in,
+                               computes, copies out and synchronises. */
+#define DD_SUBBAND 0x2u     /* use the two-stage sub-band method (needs
+                               dd_plan_set_subband) instead of direct */
+
+typedef struct dd_plan_s *dd_plan;
+typedef struct dd_stream_s *dd_stream;
+typedef struct dd_batch_s *dd_batch;
+
+/* Human-readable name of a status code (static string). */
+const char *dd_status_string(dd_status status);
+
+/* ---- plan: the problem statement of Sec. 2.1 (nu0, dnu, dtau, N_nu, DM(d)) */
+
+/* Create a plan for nchans channels sampled every dt_s seconds, channel 0
+ * at f0_mhz and channel spacing df_mhz (must be < 0: a descending band with
+ * channel 0 the highest frequency, so that every delay of Eq. 3-4 is >= 0;
+ * the lowest channel f0_mhz + (nchans-1)*df_mhz must stay > 0).
+ * Binds the plan to the current CUDA device (no device memory is touched
+ * until the first execute). */
+dd_status dd_plan_create(dd_plan *plan, int nchans, double dt_s, double f0_mhz,
+                         double df_mhz);
+
+/* Release the plan and every device buffer it owns.  NULL is a no-op. */
+void dd_plan_destroy(dd_plan plan);
+
+/* Set the trial DMs (pc cm^-3): ndm >= 1 values, non-negative and
+ * non-decreasing.  Copied; rebuilds the delay table of Eq. 4. */
+dd_status dd_plan_set_dm_list(dd_plan plan, const double *dms, int ndm);
+
+/* Generate trial DMs on [dm_lo, dm_hi) by the bounded-smearing rule read
+ * from Sec. 5.2 (the paper gives only its outcome: 1196 trials for
+ * 0 <= DM < 1000 with the HTRU band).  With t_s = dt in us, w =
+ * pulse_width_us, nu_c the mean channel frequency in GHz,
+ * a = 2 k_DM |dnu| / nu_c^3 * 1e-3 (us per unit DM) and b = a * nchans / 4,
+ * DM_0 = dm_lo and DM_{i+1} is the larger root x of
+ *   t_s^2 + w^2 + a^2 x^2 + b^2 (x - DM_i)^2 = tol^2 (t_s^2 + w^2 + a^2 DM_i^2).
+ * tol > 1 (1.25 in the benchmarks). */
+dd_status dd_plan_generate_dm_list(dd_plan plan, double dm_lo, double dm_hi,
+                                   double pulse_width_us, double tol);
+
+/* Channel kill mask of Sec. 2.3: nchans bytes, 0 = drop, nonzero = keep.
+ * NULL keeps every channel.  Copied. */
+dd_status dd_plan_set_killmask(dd_plan plan, const uint8_t *mask);
+
+/* Largest nsamps_out the plan will be executed with; sizes the device
+ * workspace up front (execute grows it on demand otherwise). */
+dd_status dd_plan_set_gulp(dd_plan plan, int64_t gulp_samples);
+
+/* Enable the sub-band method of Sec. 4.1: chans_per_subband (N') must
+ * divide nchans; dms_per_nominal (N'_DM) >= 1.  0, 0 disables it. */
+dd_status dd_plan_set_subband(dd_plan plan, int chans_per_subband,
+                              int dms_per_nominal);
+
+/* Kernel tiling: trials per thread block (16, 32 or 64), channels staged
+ * per pass (multiple of 4, <= 32) and output words per lane (2 or 4);
+ * 0 selects the built-in default for each.  The autotuner below sets these. */
+dd_status dd_plan_set_tuning(dd_plan plan, int dms_per_block, int chans_per_chunk,
+                             int words_per_lane);
+dd_status dd_plan_get_tuning(dd_plan plan, int *dms_per_block, int *chans_per_chunk,
+                             int *words_per_lane);
+
+/* Time every tiling candidate on nsamps_out synthetic samples of in_nbits
+ * and keep the fastest (Sec. 2.3 and 4.3 tuned block shape by hand; this
+ * searches the same kind of knobs).  Allocates temporary device buffers;
+ * synchronises cuda_stream. */
+dd_status dd_plan_autotune(dd_plan plan, int in_nbits, int64_t nsamps_out,
+                           void *cuda_stream);
+
+dd_status dd_plan_get_dm_count(dd_plan plan, int32_t *ndm);
+/* Copies ndm doubles. */
+dd_status dd_plan_get_dm_list(dd_plan plan, double *dms);
+/* Largest delay(d, c) of Eq. 4: the input needs nsamps_out + max_delay rows. */
+dd_status dd_plan_get_max_delay(dd_plan plan, int32_t *max_delay);
+/* Rows beyond nsamps_out that the sub-band path reads:
+ * max_{d,c} delay(gn(d), c) - delay(gn(d), n0(c)) + delay(d, n0(c)). */
+dd_status dd_plan_get_subband_max_delay(dd_plan plan, int32_t *max_delay);
+/* Copies the int32 delay table, ndm x nchans, row d = trial d. */
+dd_status dd_plan_get_delay_table(dd_plan plan, int32_t *delays);
+/* Synchronises the plan's device and returns (then clears) the OR of the
+ * device-side bound flags of every launch since the last call; 0 = clean. */
+dd_status dd_plan_get_device_status(dd_plan plan, uint32_t *flags);
+
+/* Kernel timing (tracing): while enabled, every kernel the plan launches is
+ * bracketed by CUDA events on its own stream.  get_kernel_timing synchronises
+ * on those events and returns the device time (ms) and launch count of one
+ * kernel kind since the last reset: kind 0 = corner turn (unpack/transpose
+ * into the staged image), 1 = dedispersion kernel.  reset clears both. */
+#define DD_KERNEL_CORNER_TURN 0
+#define DD_KERNEL_DEDISP 1
+dd_status dd_plan_set_kernel_timing(dd_plan plan, int enable);
+dd_status dd_plan_get_kernel_timing(dd_plan plan, int kind, double *total_ms,
+                                    int64_t *launches);
+dd_status dd_plan_reset_kernel_timing(dd_plan plan);
+
+/* ---- execute: one gulp */
+
+/* Dedisperse nsamps_out output samples per trial.  The input must hold
+ * nsamps_out + max_delay rows (sub-band: + subband max_delay).  out gets
+ * ndm rows of nsamps_out samples, row stride out_row_stride_elems
+ * (>= nsamps_out).  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).  See DD_DEVICE_PTRS for host vs device pointers. */
+dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void *in, int in_nbits,
+                     int64_t in_row_stride_bytes, void *out,
+                     int64_t out_row_stride_elems, void *cuda_stream, unsigned flags);
+
+/* ---- streaming: consecutive gulps of one beam (the overlap of Eq. 2) */
+
+/* A stream keeps the last max_delay input rows of its beam resident on the
+ * device, so that pushed gulps are dedispersed as one continuous series:
+ * the concatenation of every push's output equals dd_execute over the
+ * concatenated input.  Output sample k of the series needs input rows up
+ * to k + max_delay, so outputs lag the input by max_delay samples.
+ * max_gulp bounds nsamps_in per push.  The plan must outlive the stream. */
+dd_status dd_stream_create(dd_stream *stream, dd_plan plan, int in_nbits,
+                           int64_t max_gulp);
+void dd_stream_destroy(dd_stream stream);
+
+/* Append nsamps_in input rows and write every output sample that became
+ * computable (*nsamps_out of them, nsamps_in once the stream is primed) to
+ * out (row stride out_row_stride_elems, capacity >= nsamps_in per row). */
+dd_status dd_stream_push(dd_stream stream, const void *in, int64_t nsamps_in,
+                         int64_t in_row_stride_bytes, void *out,
+                         int64_t out_row_stride_elems, int64_t *nsamps_out,
+                         void *cuda_stream, unsigned flags);
+
+/* Samples pushed and produced so far. */
+dd_status dd_stream_position(dd_stream stream, int64_t *samples_in,
+                             int64_t *samples_out);
+
+/* Checkpoint: the stream state is (samples in, samples out, resident tail
+ * rows).  snapshot_size gives the bytes needed; snapshot copies the state
+ * into a host buffer (synchronising); restore loads one written by a stream
+ * of the same plan shape and nbits. */
+dd_status dd_stream_snapshot_size(dd_stream stream, int64_t *bytes);
+dd_status dd_stream_snapshot(dd_stream stream, void *host_buf, int64_t bytes);
+dd_status dd_stream_restore(dd_stream stream, const void *host_buf, int64_t bytes);
+
+/* ---- batch: pushes of several streams in one persistent launch */
+
+/* Collects stream pushes (device pointers only) and runs the transform of
+ * all of them in a single launch: the work of every beam - different
+ * channel counts, gulp lengths and DM lists, same in_nbits - is one list
+ * of (beam, trial block, time tile) items.  Results equal per-stream
+ * dd_stream_push bit for bit. */
+dd_status dd_batch_create(dd_batch *batch);
+void dd_batch_destroy(dd_batch batch);
+dd_status dd_batch_clear(dd_batch batch);
+dd_status dd_batch_add(dd_batch batch, dd_stream stream, const void *in_dev,
+                       int64_t nsamps_in, int64_t in_row_stride_bytes, void *out_dev,
+                       int64_t out_row_stride_elems);
+/* Launch everything added since the last clear on cuda_stream
+ * (asynchronous); nsamps_out[i] receives the outputs of the i-th add. */
+dd_status dd_batch_launch(dd_batch batch, void *cuda_stream, int64_t *nsamps_out);
+
+/* ---- measurement */
+
+/* Integer-add throughput of the current device, measured by a kernel of
+ * independent 32-bit add chains (counted one per scalar add); the compute
+ * roof of the roofline.  Synchronises. */
+dd_status dd_probe_int_add(int64_t adds_per_thread, void *cuda_stream,
+                           double *adds_per_second, double *kernel_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_DEDISP_H */

@@ -1,0 +1,444 @@
+// Direct dedispersion kernel (Sec. 2, Eq. 2) for sm_103a.
+//
+// One thread block owns a tile of B = NWARP*DPW adjacent trials x T output
+// samples of one work item and walks the channels in chunks of `cc`.  For
+// each chunk it stages, per channel, the window of the channel's image row
+// that any of its B trials needs (the temporal caching of Sec. 2.3, the
+// staged tile serving the whole trial block), as SPW copies shifted by one
+// lane each, so that for every (trial, channel) pair a warp reads its 32*K
+// words with plain conflict-free 32-bit shared loads at a word-aligned
+// offset.  Lanes of a word are summed lane-parallel (the bit-level
+// parallelism of Sec. 2.3): 4-bit lanes take 4 channels of 2-bit data (5
+// fit, 85 in 8-bit lanes), then widen to 8-, 16- and if needed 32-bit lanes,
+// so integer sums stay exact.  The kill mask is folded into the image
+// (masked rows are zero), the arithmetic form of Sec. 2.3.
+//
+// Lane layout: warp w handles trials d0 + w*DPW + i (i < DPW); lane l handles
+// words l + 32*j (j < K) of the tile, i.e. samples t0 + SPW*(l+32j) + 0..SPW-1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dd_internal.h"
+
+namespace dd {
+
+template <int FMT> struct FmtT;
+template <> struct FmtT<FMT_NIB> { static constexpr int SPW = 8, LW = 4; };
+template <> struct FmtT<FMT_BYTE> { static constexpr int SPW = 4, LW = 8; };
+template <> struct FmtT<FMT_HALF> { static constexpr int SPW = 2, LW = 16; };
+template <> struct FmtT<FMT_U32> { static constexpr int SPW = 1, LW = 32; };
+template <> struct FmtT<FMT_F32> { static constexpr int SPW = 1, LW = 32; };
+
+// ---------------------------------------------------------------------------
+// Per-word accumulators.  flush0/1/2 move a level into the next wider one;
+// final() returns the SPW exact sums of the word in time order.
+// ---------------------------------------------------------------------------
+template <int FMT, bool WIDE> struct Acc;
+
+// 4-bit lanes: n holds samples 0..7 of the word.  b0 = samples {0,2,4,6} and
+// b1 = {1,3,5,7} in 8-bit lanes; h0 = {0,4}, h1 = {2,6}, h2 = {1,5},
+// h3 = {3,7} in 16-bit lanes; u[] = 32-bit sums when WIDE.
+template <bool WIDE> struct Acc<FMT_NIB, WIDE> {
+  uint32_t n, b0, b1, h0, h1, h2, h3;
+  uint32_t u[WIDE ? 8 : 1];
+  __device__ __forceinline__ void zero() {
+    n = b0 = b1 = h0 = h1 = h2 = h3 = 0u;
+#pragma unroll
+    for (int i = 0; i < (WIDE ? 8 : 1); ++i) u[i] = 0u;
+  }
+  __device__ __forceinline__ void add4(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
+    n = n + x0 + x1;
+    n = n + x2 + x3;
+  }
+  __device__ __forceinline__ void flush0() {
+    b0 += n & 0x0F0F0F0Fu;
+    b1 += (n >> 4) & 0x0F0F0F0Fu;
+    n = 0u;
+  }
+  __device__ __forceinline__ void flush1() {
+    h0 += b0 & 0x00FF00FFu;
+    h1 += (b0 >> 8) & 0x00FF00FFu;
+    h2 += b1 & 0x00FF00FFu;
+    h3 += (b1 >> 8) & 0x00FF00FFu;
+    b0 = b1 = 0u;
+  }
+  __device__ __forceinline__ void flush2() {
+    if (WIDE) {
+      u[0] += h0 & 0xFFFFu; u[4] += h0 >> 16;
+      u[2] += h1 & 0xFFFFu; u[6] += h1 >> 16;
+      u[1] += h2 & 0xFFFFu; u[5] += h2 >> 16;
+      u[3] += h3 & 0xFFFFu; u[7] += h3 >> 16;
+      h0 = h1 = h2 = h3 = 0u;
+    }
+  }
+  __device__ __forceinline__ void final(uint32_t v[8]) {
+    flush0();
+    flush1();
+    if (WIDE) {
+      flush2();
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = u[WIDE ? i : 0];
+    } else {
+      v[0] = h0 & 0xFFFFu; v[4] = h0 >> 16;
+      v[2] = h1 & 0xFFFFu; v[6] = h1 >> 16;
+      v[1] = h2 & 0xFFFFu; v[5] = h2 >> 16;
+      v[3] = h3 & 0xFFFFu; v[7] = h3 >> 16;
+    }
+  }
+};
+
+// 8-bit lanes: b holds samples 0..3; h0 = {0,2}, h1 = {1,3} in 16-bit lanes.
+template <bool WIDE> struct Acc<FMT_BYTE, WIDE> {
+  uint32_t b, h0, h1;
+  uint32_t u[WIDE ? 4 : 1];
+  __device__ __forceinline__ void zero() {
+    b = h0 = h1 = 0u;
+#pragma unroll
+    for (int i = 0; i < (WIDE ? 4 : 1); ++i) u[i] = 0u;
+  }
+  __device__ __forceinline__ void add4(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
+    b = b + x0 + x1;
+    b = b + x2 + x3;
+  }
+  __device__ __forceinline__ void flush0() {
+    h0 += b & 0x00FF00FFu;
+    h1 += (b >> 8) & 0x00FF00FFu;
+    b = 0u;
+  }
+  __device__ __forceinline__ void flush1() {
+    if (WIDE) {
+      u[0] += h0 & 0xFFFFu; u[2] += h0 >> 16;
+      u[1] += h1 & 0xFFFFu; u[3] += h1 >> 16;
+      h0 = h1 = 0u;
+    }
+  }
+  __device__ __forceinline__ void flush2() {}
+  __device__ __forceinline__ void final(uint32_t v[4]) {
+    flush0();
+    if (WIDE) {
+      flush1();
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = u[WIDE ? i : 0];
+    } else {
+      v[0] = h0 & 0xFFFFu; v[2] = h0 >> 16;
+      v[1] = h1 & 0xFFFFu; v[3] = h1 >> 16;
+    }
+  }
+};
+
+// 16-bit lanes: h holds samples 0..1.
+template <bool WIDE> struct Acc<FMT_HALF, WIDE> {
+  uint32_t h;
+  uint32_t u[WIDE ? 2 : 1];
+  __device__ __forceinline__ void zero() {
+    h = 0u;
+#pragma unroll
+    for (int i = 0; i < (WIDE ? 2 : 1); ++i) u[i] = 0u;
+  }
+  __device__ __forceinline__ void add4(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
+    h = h + x0 + x1;
+    h = h + x2 + x3;
+  }
+  __device__ __forceinline__ void flush0() {
+    if (WIDE) {
+      u[0] += h & 0xFFFFu;
+      u[WIDE ? 1 : 0] += h >> 16;
+      h = 0u;
+    }
+  }
+  __device__ __forceinline__ void flush1() {}
+  __device__ __forceinline__ void flush2() {}
+  __device__ __forceinline__ void final(uint32_t v[2]) {
+    if (WIDE) {
+      flush0();
+      v[0] = u[0];
+      v[1] = u[WIDE ? 1 : 0];
+    } else {
+      v[0] = h & 0xFFFFu;
+      v[1] = h >> 16;
+    }
+  }
+};
+
+template <bool WIDE> struct Acc<FMT_U32, WIDE> {
+  uint32_t s;
+  __device__ __forceinline__ void zero() { s = 0u; }
+  __device__ __forceinline__ void add4(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
+    s = s + x0 + x1;
+    s = s + x2 + x3;
+  }
+  __device__ __forceinline__ void flush0() {}
+  __device__ __forceinline__ void flush1() {}
+  __device__ __forceinline__ void flush2() {}
+  __device__ __forceinline__ void final(uint32_t v[1]) { v[0] = s; }
+};
+
+// Float: channels are summed into a partial over 32 channels (8 groups),
+// then the partial is added into the total (bounds the FP32 error to about
+// 64 ulp of sum|A| rather than 1024).
+template <bool WIDE> struct Acc<FMT_F32, WIDE> {
+  float p, s;
+  __device__ __forceinline__ void zero() { p = s = 0.f; }
+  __device__ __forceinline__ void add4(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
+    p = __fadd_rn(p, __uint_as_float(x0));
+    p = __fadd_rn(p, __uint_as_float(x1));
+    p = __fadd_rn(p, __uint_as_float(x2));
+    p = __fadd_rn(p, __uint_as_float(x3));
+  }
+  __device__ __forceinline__ void flush0() {
+    s = __fadd_rn(s, p);
+    p = 0.f;
+  }
+  __device__ __forceinline__ void flush1() {}
+  __device__ __forceinline__ void flush2() {}
+  __device__ __forceinline__ void final(uint32_t v[1]) {
+    flush0();
+    v[0] = __float_as_uint(s);
+  }
+};
+
+__device__ __forceinline__ int find_seg(const LaunchParams& p, int64_t item) {
+  int lo = 0, hi = p.n_segs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (p.segs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int FMT, int OUTK, bool WIDE, int NWARP, int DPW, int K>
+__global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(const LaunchParams p) {
+  constexpr int SPW = FmtT<FMT>::SPW;
+  constexpr int LW = FmtT<FMT>::LW;
+  constexpr int NT = NWARP * 32;
+  constexpr int B = NWARP * DPW;
+  constexpr int T = 32 * K * SPW;
+
+  extern __shared__ uint4 smem4[];
+  uint32_t* s_copy = reinterpret_cast<uint32_t*>(smem4);
+  const int cc = p.cc;
+  const int nww = p.nww;
+  uint32_t* s_addr = s_copy + (size_t)cc * SPW * nww;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+
+  for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+    const Seg& S = p.segs[find_seg(p, item)];
+    const int64_t li = item - S.item_begin;
+    const int n_dmblk = S.n_dmblk;
+    const int64_t per_tile = (int64_t)S.n_groups * n_dmblk;
+    const int64_t tile = li / per_tile;
+    const int64_t rem = li - tile * per_tile;
+    const int grp = (int)(rem / n_dmblk);
+    const int blk = (int)(rem - (int64_t)grp * n_dmblk);
+    const int d0 = blk * B;
+    const int ndm_g = (grp == S.n_groups - 1) ? S.ndm_last : S.ndm;
+    const int nd = min(B, ndm_g - d0);
+    const int64_t t0 = tile * T;
+    const int64_t t_end = min(t0 + T, S.nsamps);
+    const int nchan = S.nchan;
+    const int dstride = S.delay_stride;
+    const int lo_slack = S.lo_slack;
+    const int64_t row_words = S.row_words;
+    const int32_t* __restrict__ delays = S.delays + (int64_t)grp * S.g_delay;
+    const uint32_t* __restrict__ img = S.img + (int64_t)grp * S.g_img;
+    uint32_t* const out_g = reinterpret_cast<uint32_t*>(S.out) + (int64_t)grp * S.g_out;
+    if (nd <= 0 || t0 >= S.nsamps) {
+      if (tid == 0) atomicOr(p.status, DEV_BAD_ITEM);
+      continue;
+    }
+
+    Acc<FMT, WIDE> acc[DPW][K];
+#pragma unroll
+    for (int i = 0; i < DPW; ++i)
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc[i][j].zero();
+    int g0 = 0, g1 = 0, g2 = 0;
+
+    for (int c0 = 0; c0 < nchan; c0 += cc) {
+      // (a) word address of each (trial slot, channel) window in the copies
+      for (int e = tid; e < B * cc; e += NT) {
+        const int slot = e / cc;
+        const int c = e - slot * cc;
+        const int cabs = c0 + c;
+        uint32_t a = (uint32_t)(c * SPW) * (uint32_t)nww;
+        if (cabs < nchan) {
+          const int d = d0 + min(slot, nd - 1);
+          const int64_t s0 = __ldg(&delays[(int64_t)d0 * dstride + cabs]);
+          const int64_t s = __ldg(&delays[(int64_t)d * dstride + cabs]);
+          const int64_t base = ((t0 + kPad + s0 - lo_slack) / (4 * SPW)) * (4 * SPW);
+          const int64_t o = t0 + kPad + s - base;
+          const int kap = (int)(o % SPW);
+          int64_t om = o / SPW;
+          if (o < 0 || om + 32 * K > nww) {
+            atomicOr(p.status, DEV_BAD_WINDOW);
+            om = 0;
+          }
+          a = (uint32_t)(c * SPW + kap) * (uint32_t)nww + (uint32_t)om;
+        }
+        s_addr[e] = a;
+      }
+      // (b) stage the chunk: SPW lane-shifted copies of each channel window
+      {
+        const int nq = nww >> 2;
+        for (int e = tid; e < cc * nq; e += NT) {
+          const int c = e / nq;
+          const int q = e - c * nq;
+          const int cabs = c0 + c;
+          uint4 w = make_uint4(0u, 0u, 0u, 0u);
+          uint32_t w4 = 0u;
+          if (cabs < nchan) {
+            const int64_t s0 = __ldg(&delays[(int64_t)d0 * dstride + cabs]);
+            const int64_t base = ((t0 + kPad + s0 - lo_slack) / (4 * SPW)) * (4 * SPW);
+            const int64_t wi = base / SPW + 4 * q;
+            const uint32_t* row = img + (int64_t)cabs * row_words;
+            if (wi >= 0 && wi + 4 < row_words) {
+              w = __ldg(reinterpret_cast<const uint4*>(row + wi));
+              w4 = __ldg(row + wi + 4);
+            } else {
+              atomicOr(p.status, DEV_BAD_READ);
+            }
+          }
+          uint32_t* dst = s_copy + (size_t)(c * SPW) * nww + 4 * q;
+#pragma unroll
+          for (int kap = 0; kap < SPW; ++kap) {
+            uint4 v;
+            if (kap == 0) {
+              v = w;
+            } else {
+              v.x = __funnelshift_r(w.x, w.y, kap * LW);
+              v.y = __funnelshift_r(w.y, w.z, kap * LW);
+              v.z = __funnelshift_r(w.z, w.w, kap * LW);
+              v.w = __funnelshift_r(w.w, w4, kap * LW);
+            }
+            *reinterpret_cast<uint4*>(dst + (size_t)kap * nww) = v;
+          }
+        }
+      }
+      __syncthreads();
+      // (c) shift-and-sum over the chunk, four channels per group
+      for (int cg = 0; cg < cc; cg += 4) {
+#pragma unroll
+        for (int i = 0; i < DPW; ++i) {
+          const uint4 a4 = *reinterpret_cast<const uint4*>(s_addr + (warp * DPW + i) * cc + cg);
+          const uint32_t* q0 = s_copy + a4.x + lane;
+          const uint32_t* q1 = s_copy + a4.y + lane;
+          const uint32_t* q2 = s_copy + a4.z + lane;
+          const uint32_t* q3 = s_copy + a4.w + lane;
+#pragma unroll
+          for (int j = 0; j < K; ++j)
+            acc[i][j].add4(q0[32 * j], q1[32 * j], q2[32 * j], q3[32 * j]);
+        }
+        if (++g0 == p.f0) {
+          g0 = 0;
+#pragma unroll
+          for (int i = 0; i < DPW; ++i)
+#pragma unroll
+            for (int j = 0; j < K; ++j) acc[i][j].flush0();
+          if (++g1 == p.f1) {
+            g1 = 0;
+#pragma unroll
+            for (int i = 0; i < DPW; ++i)
+#pragma unroll
+              for (int j = 0; j < K; ++j) acc[i][j].flush1();
+            if (WIDE && ++g2 == p.f2) {
+              g2 = 0;
+#pragma unroll
+              for (int i = 0; i < DPW; ++i)
+#pragma unroll
+                for (int j = 0; j < K; ++j) acc[i][j].flush2();
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    // (d) exact sums out: u32 rows, float rows, or 16-bit image rows
+#pragma unroll
+    for (int i = 0; i < DPW; ++i) {
+      const int slot = warp * DPW + i;
+      if (slot >= nd) continue;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        uint32_t v[SPW];
+        acc[i][j].final(v);
+        const int64_t tw = t0 + (int64_t)SPW * (lane + 32 * j);
+        if (OUTK == OUT_HALFIMG) {
+          uint32_t* dst = out_g + (int64_t)(d0 + slot) * S.out_stride + (tw >> 1);
+          if (SPW == 8) {
+            *reinterpret_cast<uint4*>(dst) =
+                make_uint4(v[0] | (v[1 % SPW] << 16), v[2 % SPW] | (v[3 % SPW] << 16),
+                           v[4 % SPW] | (v[5 % SPW] << 16), v[6 % SPW] | (v[7 % SPW] << 16));
+          } else if (SPW == 4) {
+            *reinterpret_cast<uint2*>(dst) =
+                make_uint2(v[0] | (v[1 % SPW] << 16), v[2 % SPW] | (v[3 % SPW] << 16));
+          } else if (SPW == 2) {
+            dst[0] = v[0] | (v[1 % SPW] << 16);
+          }
+        } else {
+          uint32_t* dst = out_g + (int64_t)(d0 + slot) * S.out_stride + tw;
+          if (p.vec_out && SPW >= 4 && tw + SPW <= t_end) {
+#pragma unroll
+            for (int q = 0; q < SPW / 4; ++q)
+              reinterpret_cast<uint4*>(dst)[q] =
+                  make_uint4(v[(4 * q) % SPW], v[(4 * q + 1) % SPW], v[(4 * q + 2) % SPW],
+                             v[(4 * q + 3) % SPW]);
+          } else if (p.vec_out && SPW == 2 && tw + 2 <= t_end) {
+            *reinterpret_cast<uint2*>(dst) = make_uint2(v[0], v[1 % SPW]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < SPW; ++e)
+              if (tw + e < t_end) dst[e] = v[e];
+          }
+        }
+      }
+    }
+  }
+}
+
+// Host helpers used by the per-format translation units.
+template <int FMT, int OUTK, bool WIDE, int NWARP, int DPW, int K>
+cudaError_t launch_one(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
+  auto kern = k_dedisp<FMT, OUTK, WIDE, NWARP, DPW, K>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, NWARP * 32, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int FMT, int OUTK, bool WIDE, int NWARP, int DPW, int K>
+cudaError_t occupancy_one(size_t smem, int* nblk) {
+  auto kern = k_dedisp<FMT, OUTK, WIDE, NWARP, DPW, K>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nblk, kern, NWARP * 32, smem);
+}
+
+// Dispatch over the compiled tile shapes for one (FMT, OUTK, WIDE).
+template <int FMT, int OUTK, bool WIDE>
+cudaError_t dispatch_cfg(int cfg, const LaunchParams* p, int grid, size_t smem,
+                         cudaStream_t st, int* occ) {
+  switch (cfg) {
+#define DD_CFG_CASE(I)                                                                   \
+  case I:                                                                                \
+    return occ ? occupancy_one<FMT, OUTK, WIDE, kTileCfgs[I].nwarp, kTileCfgs[I].dpw,     \
+                               kTileCfgs[I].k>(smem, occ)                                \
+               : launch_one<FMT, OUTK, WIDE, kTileCfgs[I].nwarp, kTileCfgs[I].dpw,        \
+                            kTileCfgs[I].k>(*p, grid, smem, st);
+    DD_CFG_CASE(0)
+    DD_CFG_CASE(1)
+    DD_CFG_CASE(2)
+#undef DD_CFG_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace dd

@@ -1,0 +1,498 @@
+// Execution: corner turn into the staged image, then the direct kernel over
+// a list of work segments (direct: one segment; sub-band: one segment per
+// sub-band for stage 1 and one per trial group for stage 2, Sec. 4.1).
+#include <dlfcn.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+
+#include "dd_internal.h"
+
+namespace dd {
+
+int fmt_for_nbits(int nbits) {
+  switch (nbits) {
+    case 1:
+    case 2: return FMT_NIB;
+    case 4: return FMT_BYTE;
+    case 8: return FMT_HALF;
+    case 32: return FMT_F32;
+    default: return -1;
+  }
+}
+
+int vmax_for_nbits(int nbits) { return nbits == 32 ? 0 : (1 << nbits) - 1; }
+
+// Largest staging spread of any (trial block, channel): max_d delay(d,c) -
+// delay(d0,c) + lo_slack, where lo_slack covers trials whose delay is below
+// the block's first (sub-band stage-1 tables are only nearly monotone).
+int32_t max_block_spread(const int32_t* delays, int ndm, int nchans, int stride, int B,
+                         int32_t* lo_slack) {
+  int32_t spread = 0, lo = 0;
+  for (int d0 = 0; d0 < ndm; d0 += B) {
+    const int d1 = std::min(ndm, d0 + B);
+    for (int c = 0; c < nchans; ++c) {
+      const int32_t s0 = delays[(size_t)d0 * stride + c];
+      int32_t mn = s0, mx = s0;
+      for (int d = d0 + 1; d < d1; ++d) {
+        const int32_t s = delays[(size_t)d * stride + c];
+        mn = std::min(mn, s);
+        mx = std::max(mx, s);
+      }
+      lo = std::max(lo, s0 - mn);
+      spread = std::max(spread, mx - s0);
+    }
+  }
+  *lo_slack = lo;
+  return spread + lo;
+}
+
+int time_tile(int fmt, const Tuning& t) { return 32 * t.words_per_lane * fmt_spw(fmt); }
+
+static int window_words(int fmt, const Tuning& t, int32_t spread) {
+  const int spw = fmt_spw(fmt);
+  int nww = (4 * spw - 1 + spread) / spw + 32 * t.words_per_lane;
+  return (nww + 3) & ~3;
+}
+
+// Image row pitch (words) covering every staging read of a job with nsamps
+// outputs, largest delay maxd and staging spread `spread`.
+int64_t image_row_words(int fmt, const Tuning& t, int64_t nsamps, int32_t maxd,
+                        int32_t spread) {
+  const int spw = fmt_spw(fmt);
+  const int T = time_tile(fmt, t);
+  const int64_t tiles = (nsamps + T - 1) / T;
+  const int64_t last_sample = tiles * T + kPad + maxd + 4 * spw;
+  int64_t w = last_sample / spw + window_words(fmt, t, spread) + 8;
+  return (w + 31) & ~(int64_t)31;
+}
+
+static void flush_periods(int fmt, int vmax, int nchan_max, bool* wide, int* f0, int* f1,
+                          int* f2) {
+  *wide = false;
+  *f0 = *f1 = *f2 = INT_MAX;
+  if (vmax < 1) vmax = 1;
+  switch (fmt) {
+    case FMT_NIB:
+      *f0 = std::max(1, 15 / (4 * vmax));
+      *f1 = std::max(1, 255 / (4 * vmax * *f0));
+      *f2 = std::max(1, 65535 / (4 * vmax * *f0 * *f1));
+      *wide = (int64_t)nchan_max * vmax > 65535;
+      break;
+    case FMT_BYTE:
+      *f0 = std::max(1, 255 / (4 * vmax));
+      *f1 = std::max(1, 65535 / (4 * vmax * *f0));
+      *wide = (int64_t)nchan_max * vmax > 65535;
+      break;
+    case FMT_HALF:
+      *f0 = std::max(1, 65535 / (4 * vmax));
+      *wide = (int64_t)nchan_max * vmax > 65535;
+      break;
+    case FMT_F32:
+      *f0 = 8;  // 32 channels per FP32 partial sum
+      break;
+    default:
+      break;
+  }
+}
+
+struct SegSpec {
+  Seg seg;
+  int32_t spread;
+};
+
+// Fill launch parameters for a set of segments sharing one staged format.
+static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector<SegSpec>& specs,
+                               bool vec_out, LaunchPlan* L) {
+  const int cfg = tile_cfg_index(p.tune);
+  const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
+  const int T = time_tile(fmt, p.tune);
+  int32_t spread = 0;
+  int nchan_max = 0;
+  for (auto& s : specs) {
+    spread = std::max(spread, s.spread);
+    nchan_max = std::max(nchan_max, (int)s.seg.nchan);
+  }
+  const int nww = window_words(fmt, p.tune, spread);
+  int cc = p.tune.chans_per_chunk;
+  const size_t smem_cap = 220 * 1024;
+  while (cc > 4 && dedisp_smem_bytes(fmt, cfg, cc, nww) > smem_cap) cc -= 4;
+  if (dedisp_smem_bytes(fmt, cfg, cc, nww) > smem_cap) return DD_ERR_INVALID_ARG;
+
+  L->fmt = fmt;
+  L->outk = outk;
+  L->cfg = cfg;
+  L->segs.clear();
+  int64_t items = 0;
+  for (auto& s : specs) {
+    Seg g = s.seg;
+    if (g.n_groups < 1) g.n_groups = 1;
+    if (g.ndm_last <= 0) g.ndm_last = g.ndm;
+    if (g.ndm <= 0 || g.nsamps <= 0) continue;
+    g.n_dmblk = (g.ndm + B - 1) / B;
+    const int64_t tiles = (g.nsamps + T - 1) / T;
+    g.item_begin = items;
+    items += (int64_t)g.n_dmblk * g.n_groups * tiles;
+    L->segs.push_back(g);
+  }
+  if (L->segs.size() > (size_t)kMaxSegs) return DD_ERR_INVALID_ARG;
+  bool wide;
+  int f0, f1, f2;
+  flush_periods(fmt, vmax, nchan_max, &wide, &f0, &f1, &f2);
+  if (outk == OUT_HALFIMG && (wide || (int64_t)nchan_max * std::max(vmax, 1) > 65535))
+    return DD_ERR_OVERFLOW;
+  L->wide = wide;
+  LaunchParams& lp = L->lp;
+  std::memset(&lp, 0, sizeof(lp));
+  lp.n_segs = (int32_t)L->segs.size();
+  for (size_t i = 0; i < L->segs.size(); ++i) lp.segs[i] = L->segs[i];
+  lp.nww = nww;
+  lp.cc = cc;
+  lp.f0 = f0;
+  lp.f1 = f1;
+  lp.f2 = f2;
+  lp.n_items = items;
+  lp.vec_out = vec_out ? 1 : 0;
+  L->smem = dedisp_smem_bytes(fmt, cfg, cc, nww);
+  int per_sm = 0;
+  cudaError_t e = dedisp_max_blocks_per_sm(fmt, outk, wide, cfg, L->smem, &per_sm);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (per_sm < 1) return DD_ERR_INVALID_ARG;
+  const int64_t resident = (int64_t)per_sm * std::max(1, p.num_sms);
+  L->grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, resident));
+  return DD_OK;
+}
+
+dd_status run_launch(Plan& p, LaunchPlan& L, cudaStream_t st) {
+  if (L.lp.n_items == 0) return DD_OK;
+  L.lp.status = static_cast<uint32_t*>(p.d_status.p);
+  KernelTimer kt(&p, 1, st);
+  return cuda_status(launch_dedisp(L.fmt, L.outk, L.wide, L.cfg, L.lp, L.grid, L.smem, st));
+}
+
+dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
+                             const std::vector<DirectJob>& jobs, LaunchPlan* L) {
+  const int cfg = tile_cfg_index(p.tune);
+  const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
+  std::vector<SegSpec> specs;
+  bool vec = true;
+  for (const DirectJob& j : jobs) {
+    SegSpec s;
+    std::memset(&s, 0, sizeof(s));
+    const int bi = b_index(B);
+    int32_t lo = j.plan->lo_B[bi];
+    s.spread = j.plan->spread_B[bi];
+    s.seg.img = j.img;
+    s.seg.delays = j.d_delays;
+    s.seg.out = j.out;
+    s.seg.row_words = j.row_words;
+    s.seg.out_stride = j.out_stride;
+    s.seg.nsamps = j.nsamps;
+    s.seg.delay_stride = j.nchans;
+    s.seg.nchan = j.nchans;
+    s.seg.ndm = j.ndm;
+    s.seg.lo_slack = lo;
+    s.seg.n_groups = 1;
+    s.seg.ndm_last = j.ndm;
+    if (lo > kPad) return DD_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(j.out) & 15) || (j.out_stride & 3)) vec = false;
+    specs.push_back(s);
+  }
+  return finish_launch(p, fmt, outk, vmax, specs, vec, L);
+}
+
+// Geometry of the staged input image for a direct job: large enough for
+// every compiled tile shape, so an image staged under one plan's tiling can
+// be dedispersed by a launch that uses another's (batches).
+static int64_t direct_row_words(Plan& p, int fmt, int64_t nsamps) {
+  int64_t rw = 0;
+  for (int i = 0; i < kNumTileCfgs; ++i) {
+    Tuning t;
+    t.dms_per_block = kTileCfgs[i].nwarp * kTileCfgs[i].dpw;
+    t.words_per_lane = kTileCfgs[i].k;
+    const int32_t spread = p.spread_B[b_index(t.dms_per_block)];
+    rw = std::max(rw, image_row_words(fmt, t, nsamps, p.max_delay, spread));
+  }
+  return rw;
+}
+
+// Best-effort check that a device buffer holds `bytes` from `ptr`, through
+// the driver's cuMemGetAddressRange (resolved at run time so that the library
+// also loads on hosts without a driver).  Unknown ranges pass.
+typedef int (*GetRangeFn)(unsigned long long*, size_t*, unsigned long long);
+static GetRangeFn get_range_fn() {
+  static GetRangeFn fn = [] {
+    void* h = dlopen("libcuda.so.1", RTLD_LAZY | RTLD_NOLOAD);
+    if (!h) h = dlopen("libcuda.so.1", RTLD_LAZY);
+    if (!h) return (GetRangeFn) nullptr;
+    void* f = dlsym(h, "cuMemGetAddressRange_v2");
+    return (GetRangeFn)f;
+  }();
+  return fn;
+}
+
+static bool device_range_ok(const void* ptr, size_t bytes) {
+  GetRangeFn fn = get_range_fn();
+  if (!fn) return true;
+  unsigned long long base = 0;
+  size_t size = 0;
+  if (fn(&base, &size, (unsigned long long)(uintptr_t)ptr) != 0) return true;
+  return (unsigned long long)(uintptr_t)ptr + bytes <= base + size;
+}
+
+// Corner-turn `rows` input rows into `image` (grown as needed); fills the
+// staged-image fields of a direct job for nsamps outputs.
+dd_status stage_direct_image(Plan& p, const void* in, int nbits, int64_t in_stride, int64_t rows,
+                             int64_t nsamps, DevBuf& image, cudaStream_t st, DirectJob* j) {
+  const int fmt = fmt_for_nbits(nbits);
+  const int64_t rw = direct_row_words(p, fmt, nsamps);
+  cudaError_t e = image.ensure((size_t)p.nchans * rw * 4);
+  if (e != cudaSuccess) return cuda_status(e);
+  uint32_t* img = static_cast<uint32_t*>(image.p);
+  {
+    KernelTimer kt(&p, 0, st);
+    e = launch_corner_turn(nbits, static_cast<const uint8_t*>(in), in_stride, 0, rows, p.nchans,
+                           static_cast<const uint8_t*>(p.d_mask.p), img, rw, rw, st);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  j->img = img;
+  j->row_words = rw;
+  j->img_row_samples = rw * fmt_spw(fmt);
+  j->d_delays = static_cast<const int32_t*>(p.d_delays.p);
+  j->h_delays = p.delays.data();
+  j->nchans = p.nchans;
+  j->ndm = ndm(p);
+  j->nsamps = nsamps;
+  j->plan = &p;
+  return DD_OK;
+}
+
+static dd_status exec_direct(Plan& p, const ExecArgs& a, int fmt) {
+  const int64_t rows = a.nsamps_out + p.max_delay;
+  DirectJob j;
+  dd_status s0 = stage_direct_image(p, a.in, a.in_nbits, a.in_row_stride, rows, a.nsamps_out,
+                                    p.d_image, a.st, &j);
+  if (s0 != DD_OK) return s0;
+  j.out = a.out;
+  j.out_stride = a.out_stride;
+  LaunchPlan L;
+  dd_status s = plan_direct_launch(p, fmt, fmt == FMT_F32 ? OUT_F32 : OUT_U32,
+                                   vmax_for_nbits(a.in_nbits), {j}, &L);
+  if (s != DD_OK) return s;
+  return run_launch(p, L, a.st);
+}
+
+static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
+  if (fmt == FMT_F32) return DD_ERR_UNSUPPORTED_NBITS;
+  dd_status s = upload_subband(p);
+  if (s != DD_OK) return s;
+  const int C = p.nchans, Np = p.sb_chans, nsb = C / Np;
+  const int n = ndm(p);
+  const int ng = (n + p.sb_dms - 1) / p.sb_dms;
+  const int cfg = tile_cfg_index(p.tune);
+  const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
+  const int vmax_in = vmax_for_nbits(a.in_nbits);
+  const int64_t G = a.nsamps_out;
+  const int64_t len1 = G + p.sb_len1_extra;  // stage-1 outputs per row
+
+  // stage-1 geometry over the relative-delay table (ng x C, per sub-band)
+  const int bi = b_index(B);
+  const int32_t spread1 = p.sb1_spread_B[bi], lo1 = p.sb1_lo_B[bi];
+  const int32_t maxrel = p.sb_maxrel;
+  if (lo1 > kPad) return DD_ERR_INVALID_ARG;
+  const int64_t rw = image_row_words(fmt, p.tune, len1, maxrel, spread1);
+  cudaError_t e = p.d_image.ensure((size_t)C * rw * 4);
+  if (e != cudaSuccess) return cuda_status(e);
+  uint32_t* img = static_cast<uint32_t*>(p.d_image.p);
+  const int64_t rows = G + p.sb_max_delay;
+  {
+    KernelTimer kt(&p, 0, a.st);
+    e = launch_corner_turn(a.in_nbits, static_cast<const uint8_t*>(a.in), a.in_row_stride, 0,
+                           rows, C, static_cast<const uint8_t*>(p.d_mask.p), img, rw, rw, a.st);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+
+  // intermediate: 16-bit image rows when stage-1 sums fit, else 32-bit
+  const int64_t vmax1 = (int64_t)Np * vmax_in;
+  const bool half = vmax1 <= 65535;
+  const int fmt2 = half ? FMT_HALF : FMT_U32;
+  const int32_t spread2 = p.sb2_spread_B[bi], lo2 = p.sb2_lo_B[bi];
+  if (lo2 > kPad) return DD_ERR_INVALID_ARG;
+  const int T1 = time_tile(fmt, p.tune);
+  const int spw2 = fmt_spw(fmt2);
+  int64_t rw2 = image_row_words(fmt2, p.tune, G, (int32_t)p.sb_len1_extra, spread2);
+  const int64_t st1_words = (kPad + ((len1 + T1 - 1) / T1) * T1) / spw2 + 8;
+  rw2 = std::max(rw2, (st1_words + 31) & ~(int64_t)31);
+  const size_t s_bytes = (size_t)ng * nsb * rw2 * 4;
+  if (p.d_sb_S.bytes < s_bytes || !p.d_sb_S.p) {
+    if ((e = p.d_sb_S.ensure(s_bytes)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(p.d_sb_S.p, 0, p.d_sb_S.bytes, a.st)) != cudaSuccess)
+      return cuda_status(e);
+  }
+  uint32_t* S = static_cast<uint32_t*>(p.d_sb_S.p);
+
+  // stage 1: sub-band n (a group of the segment) sums its N' channels at
+  // each trial group's nominal DM
+  std::vector<SegSpec> specs(1);
+  {
+    SegSpec& sp = specs[0];
+    std::memset(&sp, 0, sizeof(sp));
+    sp.spread = spread1;
+    Seg& g = sp.seg;
+    g.img = img;
+    g.row_words = rw;
+    g.delays = static_cast<const int32_t*>(p.d_sb_rel.p);
+    g.delay_stride = C;
+    g.nchan = Np;
+    g.ndm = ng;
+    g.ndm_last = ng;
+    g.n_groups = nsb;
+    g.g_img = (int64_t)Np * rw;
+    g.g_delay = Np;
+    g.g_out = rw2;
+    g.lo_slack = lo1;
+    g.nsamps = len1;
+    g.out = S + (half ? kPad / 2 : kPad);
+    g.out_stride = (int64_t)nsb * rw2;
+  }
+  LaunchPlan L1;
+  s = finish_launch(p, fmt, half ? OUT_HALFIMG : OUT_U32, vmax_in, specs, true, &L1);
+  if (s != DD_OK) return s;
+  if ((s = run_launch(p, L1, a.st)) != DD_OK) return s;
+
+  // stage 2: each trial sums the sub-bands of its group (a group of the
+  // segment), shifted by delay(d, nN')
+  {
+    SegSpec& sp = specs[0];
+    std::memset(&sp, 0, sizeof(sp));
+    sp.spread = spread2;
+    Seg& q = sp.seg;
+    q.img = S;
+    q.row_words = rw2;
+    q.delays = static_cast<const int32_t*>(p.d_sb_d2.p);
+    q.delay_stride = nsb;
+    q.nchan = nsb;
+    q.ndm = p.sb_dms;
+    q.ndm_last = n - (ng - 1) * p.sb_dms;
+    q.n_groups = ng;
+    q.g_img = (int64_t)nsb * rw2;
+    q.g_delay = p.sb_dms * nsb;
+    q.g_out = (int64_t)p.sb_dms * a.out_stride;
+    q.lo_slack = lo2;
+    q.nsamps = G;
+    q.out = a.out;
+    q.out_stride = a.out_stride;
+  }
+  const bool vec = !(reinterpret_cast<uintptr_t>(a.out) & 15) && !(a.out_stride & 3);
+  LaunchPlan L2;
+  s = finish_launch(p, fmt2, OUT_U32, (int)std::min<int64_t>(vmax1, INT_MAX), specs, vec, &L2);
+  if (s != DD_OK) return s;
+  return run_launch(p, L2, a.st);
+}
+
+dd_status exec_device(Plan& p, const ExecArgs& a) {
+  const int fmt = fmt_for_nbits(a.in_nbits);
+  if (fmt < 0) return DD_ERR_UNSUPPORTED_NBITS;
+  dd_status s = ensure_device_tables(p);
+  if (s != DD_OK) return s;
+  return a.subband ? exec_subband(p, a, fmt) : exec_direct(p, a, fmt);
+}
+
+}  // namespace dd
+
+using namespace dd;
+
+extern "C" dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void* in, int in_nbits,
+                                int64_t in_row_stride, void* out, int64_t out_stride,
+                                void* cuda_stream, unsigned flags) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p || !in || !out || nsamps_out <= 0 || out_stride < nsamps_out) return DD_ERR_INVALID_ARG;
+  const int fmt = fmt_for_nbits(in_nbits);
+  if (fmt < 0) return DD_ERR_UNSUPPORTED_NBITS;
+  if (p->dms.empty()) return DD_ERR_NO_DM_LIST;
+  const int64_t row_bytes =
+      in_nbits == 32 ? (int64_t)p->nchans * 4 : ((int64_t)p->nchans * in_nbits + 7) / 8;
+  if (in_row_stride < row_bytes) return DD_ERR_INVALID_ARG;
+  const bool sub = (flags & DD_SUBBAND) != 0;
+  if (sub && p->sb_chans <= 0) return DD_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(p->mu);
+  if (sub) {
+    dd_status s = prepare_subband(*p);
+    if (s != DD_OK) return s;
+  }
+  const int64_t rows = nsamps_out + (sub ? p->sb_max_delay : p->max_delay);
+  ExecArgs a;
+  a.nsamps_out = nsamps_out;
+  a.in_nbits = in_nbits;
+  a.in_row_stride = in_row_stride;
+  a.in_rows = rows;
+  a.out_stride = out_stride;
+  a.st = static_cast<cudaStream_t>(cuda_stream);
+  a.subband = sub;
+  const size_t in_bytes = (size_t)(rows - 1) * in_row_stride + row_bytes;
+  const size_t out_bytes = (size_t)((int64_t)(ndm(*p) - 1) * out_stride + nsamps_out) * 4;
+  if (flags & DD_DEVICE_PTRS) {
+    if (!device_range_ok(in, in_bytes)) return DD_ERR_INPUT_TOO_SHORT;
+    if (!device_range_ok(out, out_bytes)) return DD_ERR_INVALID_ARG;
+    a.in = in;
+    a.out = out;
+    return exec_device(*p, a);
+  }
+  // host pointers: stage through plan-owned device buffers
+  cudaError_t e;
+  if ((e = p->d_in.ensure(in_bytes)) != cudaSuccess) return cuda_status(e);
+  if ((e = p->d_out.ensure(out_bytes)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaMemcpyAsync(p->d_in.p, in, in_bytes, cudaMemcpyHostToDevice, a.st)) != cudaSuccess)
+    return cuda_status(e);
+  a.in = p->d_in.p;
+  a.out = p->d_out.p;
+  dd_status s = exec_device(*p, a);
+  if (s != DD_OK) return s;
+  if ((e = cudaMemcpyAsync(out, p->d_out.p, out_bytes, cudaMemcpyDeviceToHost, a.st)) !=
+      cudaSuccess)
+    return cuda_status(e);
+  if ((e = cudaStreamSynchronize(a.st)) != cudaSuccess) return cuda_status(e);
+  return DD_OK;
+}
+
+extern "C" dd_status dd_probe_int_add(int64_t adds_per_thread, void* cuda_stream,
+                                      double* adds_per_second, double* kernel_ms) {
+  if (adds_per_thread < 32 || !adds_per_second) return DD_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, sms) * 8;
+  const int64_t iters = (adds_per_thread / 8 / 4) * 4;
+  uint32_t* seed = nullptr;
+  uint32_t* sink = nullptr;
+  cudaError_t e = cudaMalloc(&seed, 16 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&sink, (size_t)grid * 256 * 4);
+  if (e != cudaSuccess) {
+    cudaFree(seed);
+    return cuda_status(e);
+  }
+  uint32_t h[16];
+  for (int i = 0; i < 16; ++i) h[i] = 0x9E3779B9u * (i + 1);
+  cudaEvent_t a = nullptr, b = nullptr;
+  float ms = 0.f;
+  e = cudaMemcpy(seed, h, sizeof(h), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = launch_probe(seed, iters, sink, grid, st);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(a, st);
+  if (e == cudaSuccess) e = launch_probe(seed, iters, sink, grid, st);
+  if (e == cudaSuccess) e = cudaEventRecord(b, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(seed);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_status(e);
+  const double adds = (double)grid * 256.0 * (double)iters * 8.0;
+  *adds_per_second = adds / (ms * 1e-3);
+  if (kernel_ms) *kernel_ms = ms;
+  return DD_OK;
+}

@@ -1,0 +1,241 @@
+// Internal declarations of the GB300 dedispersion library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dedisp.h"
+
+namespace dd {
+
+// ---------------------------------------------------------------------------
+// Staged image ("lane format").  Before dedispersion the time-major input is
+// turned into one row per channel, samples packed along time into 32-bit
+// words: word w of a row holds image samples [w*SPW, (w+1)*SPW), sample i
+// of the word in lane i (bits [i*LW, (i+1)*LW)).  Image sample s is time
+// s - kPad: a left pad keeps every staging window start non-negative.
+// Lane widths leave guard bits above the data so that several channels can
+// be added lane-parallel (the bit-level parallelism of Sec. 2.3):
+//   FMT_NIB  4-bit lanes, 8 samples/word, 1- and 2-bit input
+//   FMT_BYTE 8-bit lanes, 4 samples/word, 4-bit input
+//   FMT_HALF 16-bit lanes, 2 samples/word, 8-bit input and sub-band stage 2
+//   FMT_U32  32-bit unsigned, 1 sample/word, wide sub-band intermediates
+//   FMT_F32  32-bit float, 1 sample/word, float input
+// ---------------------------------------------------------------------------
+enum Fmt { FMT_NIB = 0, FMT_BYTE = 1, FMT_HALF = 2, FMT_U32 = 3, FMT_F32 = 4 };
+enum OutKind { OUT_U32 = 0, OUT_F32 = 1, OUT_HALFIMG = 2 };
+
+constexpr int kPad = 32;  // image samples before time 0 (multiple of 4*SPW)
+
+inline int fmt_spw(int fmt) {
+  switch (fmt) {
+    case FMT_NIB: return 8;
+    case FMT_BYTE: return 4;
+    case FMT_HALF: return 2;
+    default: return 1;
+  }
+}
+inline int fmt_lane_bits(int fmt) { return 32 / fmt_spw(fmt); }
+
+// Device status flags (OR-ed by kernels, read by dd_plan_get_device_status).
+enum : uint32_t {
+  DEV_BAD_WINDOW = 1u,  // a lane window ran past the staged copy
+  DEV_BAD_READ = 2u,    // staging read past an image row
+  DEV_BAD_ITEM = 4u,    // malformed work item
+};
+
+// One regular grid of work: n_groups groups, each `ndm` trials (`ndm_last` in
+// the last group) x nsamps outputs over one image.  Group g uses the image,
+// delay table and output advanced by g times the group strides (sub-bands in
+// sub-band stage 1, trial groups in stage 2; a direct job has one group).
+// Items of a segment are (time tile, group, trial block), trial block fastest.
+struct Seg {
+  const uint32_t* img;    // image row of channel 0 (group 0)
+  const int32_t* delays;  // delay of trial 0, channel 0 (group 0)
+  void* out;              // output row of trial 0 at time 0 (group 0)
+  int64_t row_words;      // image row pitch, words
+  int64_t out_stride;     // output row pitch (elements, or words for OUT_HALFIMG)
+  int64_t nsamps;         // outputs per trial
+  int64_t item_begin;     // first global item index of this segment
+  int64_t g_img;          // per-group image offset, words
+  int64_t g_out;          // per-group output offset, elements (words)
+  int32_t g_delay;        // per-group delay-table offset, elements
+  int32_t n_groups;       // >= 1
+  int32_t ndm;            // trials per group
+  int32_t ndm_last;       // trials in the last group
+  int32_t n_dmblk;        // ceil(ndm / trials per block)
+  int32_t delay_stride;   // elements between trial rows of the delay table
+  int32_t nchan;          // channels summed
+  int32_t lo_slack;       // max_{block,c} delay(d0,c) - min_{d in block} delay(d,c)
+};
+
+constexpr int kMaxSegs = 32;  // segments per launch, passed inline as a kernel parameter
+
+struct LaunchParams {
+  Seg segs[kMaxSegs];
+  int32_t n_segs;
+  int32_t nww;       // words per staged copy window (multiple of 4)
+  int32_t cc;        // channels per staged chunk (multiple of 4)
+  int32_t f0, f1, f2;  // flush periods (groups of 4 channels) per level
+  int64_t n_items;
+  uint32_t* status;
+  int32_t vec_out;   // 1 if every output row/tile start is 16-byte aligned
+  int32_t pad_;
+};
+
+// Kernel shapes compiled into the library.
+struct TileCfg {
+  int nwarp, dpw, k;  // warps per block, trials per warp, words per lane
+};
+constexpr TileCfg kTileCfgs[] = {{16, 2, 4}, {16, 4, 2}, {8, 2, 4}};
+constexpr int kNumTileCfgs = 3;
+
+// Host launchers (dd_kernels_*.cu).
+cudaError_t launch_dedisp(int fmt, int outk, bool wide, int cfg, const LaunchParams& p,
+                          int grid, size_t smem, cudaStream_t st);
+cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, size_t smem,
+                                     int* nblk);
+cudaError_t launch_corner_turn(int nbits, const uint8_t* in, int64_t in_stride,
+                               int64_t t_begin, int64_t nrows_valid, int nchans,
+                               const uint8_t* mask, uint32_t* img, int64_t row_words,
+                               int64_t words, cudaStream_t st);
+
+size_t dedisp_smem_bytes(int fmt, int cfg, int cc, int nww);
+cudaError_t launch_probe(const uint32_t* seed, int64_t iters, uint32_t* sink, int grid,
+                         cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf();
+  cudaError_t ensure(size_t n);  // grow-only
+  void release();
+};
+
+struct Tuning {
+  int dms_per_block = 32;
+  int chans_per_chunk = 8;
+  int words_per_lane = 4;
+};
+
+struct Plan {
+  int device = 0;
+  int nchans = 0;
+  double dt = 0, f0 = 0, df = 0;
+  std::vector<double> dms;
+  std::vector<int32_t> delays;  // ndm x nchans
+  std::vector<uint8_t> mask;    // nchans
+  int32_t max_delay = 0;
+  int64_t gulp = 0;
+  int sb_chans = 0, sb_dms = 0;  // sub-band N', N'_DM (0 = off)
+  Tuning tune;
+  bool tuned_by_search = false;
+  int num_sms = 0;
+
+  // device state
+  DevBuf d_delays, d_mask, d_status, d_image, d_in, d_out;
+  DevBuf d_sb_rel, d_sb_d2, d_sb_S;
+  bool delays_dirty = true, mask_dirty = true, sb_dirty = true, sb_dev_dirty = true;
+  std::vector<int32_t> sb_rel, sb_d2;  // host copies of the sub-band tables
+  int32_t sb_max_delay = 0;
+  int64_t sb_len1_extra = 0;  // max_{d,n} delay(d, nN')
+  // staging spreads (incl. lo_slack) and lo_slack per trials-per-block
+  // B = 16 << i, for the direct table and the two sub-band stages
+  int32_t spread_B[3] = {0, 0, 0}, lo_B[3] = {0, 0, 0};
+  int32_t sb1_spread_B[3] = {0, 0, 0}, sb1_lo_B[3] = {0, 0, 0};
+  int32_t sb2_spread_B[3] = {0, 0, 0}, sb2_lo_B[3] = {0, 0, 0};
+  int32_t sb_maxrel = 0;
+  // kernel timing (dd_plan_set_kernel_timing)
+  bool timing = false;
+  struct TimedLaunch {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<TimedLaunch> timed;
+  double timed_ms[2] = {0.0, 0.0};
+  int64_t timed_n[2] = {0, 0};
+  std::mutex mu;
+  ~Plan();
+};
+
+// Bracket a kernel launch with events when the plan's timing is enabled.
+struct KernelTimer {
+  Plan* p;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  KernelTimer(Plan* plan, int k, cudaStream_t s);
+  ~KernelTimer();
+};
+
+inline int b_index(int B) { return B <= 16 ? 0 : (B <= 32 ? 1 : 2); }
+
+int ndm(const Plan& p);
+dd_status ensure_device_tables(Plan& p);
+dd_status prepare_subband(Plan& p);  // host tables only
+dd_status upload_subband(Plan& p);   // host tables + device copies
+int tile_cfg_index(const Tuning& t);
+
+// Direct and sub-band execution on device buffers (asynchronous on st).
+struct ExecArgs {
+  int64_t nsamps_out;
+  const void* in;
+  int in_nbits;
+  int64_t in_row_stride;
+  int64_t in_rows;      // rows available in `in` (>= nsamps_out + max_delay)
+  void* out;
+  int64_t out_stride;
+  cudaStream_t st;
+  bool subband;
+};
+dd_status exec_device(Plan& p, const ExecArgs& a);
+
+// Build the segments and launch parameters for a direct transform over an
+// already staged image (used by execute, streams and batches).
+struct DirectJob {
+  const uint32_t* img;
+  int64_t row_words;
+  int64_t img_row_samples;  // valid image samples per row incl. left pad
+  const int32_t* d_delays;  // device delay table (ndm x nchans)
+  const int32_t* h_delays;  // host copy (planning)
+  int nchans;
+  int ndm;
+  int64_t nsamps;
+  void* out;
+  int64_t out_stride;
+  const Plan* plan;  // owner of the delay table (cached staging spreads)
+};
+
+struct LaunchPlan {
+  int fmt, outk, cfg;
+  bool wide;
+  LaunchParams lp;
+  std::vector<Seg> segs;
+  size_t smem;
+  int grid;
+};
+
+// Image geometry for a job of nsamps outputs with max delay maxd.
+int64_t image_row_words(int fmt, const Tuning& t, int64_t nsamps, int32_t maxd,
+                        int32_t spread);
+int32_t max_block_spread(const int32_t* delays, int ndm, int nchans, int stride,
+                         int B, int32_t* lo_slack);
+int time_tile(int fmt, const Tuning& t);
+dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
+                             const std::vector<DirectJob>& jobs, LaunchPlan* lpl);
+dd_status run_launch(Plan& p, LaunchPlan& lpl, cudaStream_t st);
+dd_status stage_direct_image(Plan& p, const void* in, int nbits, int64_t in_stride, int64_t rows,
+                             int64_t nsamps, DevBuf& image, cudaStream_t st, DirectJob* j);
+
+dd_status cuda_status(cudaError_t e);
+int fmt_for_nbits(int nbits);
+int vmax_for_nbits(int nbits);
+
+}  // namespace dd

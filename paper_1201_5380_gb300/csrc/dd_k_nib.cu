@@ -1,0 +1,16 @@
+// Instantiations of the dedispersion kernel for the FMT_NIB staged format.
+#include "dd_dedisp.cuh"
+
+namespace dd {
+
+cudaError_t dispatch_nib(int outk, bool wide, int cfg, const LaunchParams* p, int grid,
+                          size_t smem, cudaStream_t st, int* occ) {
+  if (outk == OUT_U32)
+    return wide ? dispatch_cfg<FMT_NIB, OUT_U32, true>(cfg, p, grid, smem, st, occ)
+                : dispatch_cfg<FMT_NIB, OUT_U32, false>(cfg, p, grid, smem, st, occ);
+  if (outk == OUT_HALFIMG && !wide)
+    return dispatch_cfg<FMT_NIB, OUT_HALFIMG, false>(cfg, p, grid, smem, st, occ);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace dd

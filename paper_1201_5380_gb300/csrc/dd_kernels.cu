@@ -1,0 +1,167 @@
+// Corner turn (unpack + transpose into the staged image), the integer-add
+// probe, and the format dispatch of the dedispersion kernel.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dd_internal.h"
+
+namespace dd {
+
+cudaError_t dispatch_nib(int, bool, int, const LaunchParams*, int, size_t, cudaStream_t, int*);
+cudaError_t dispatch_byte(int, bool, int, const LaunchParams*, int, size_t, cudaStream_t, int*);
+cudaError_t dispatch_half(int, bool, int, const LaunchParams*, int, size_t, cudaStream_t, int*);
+cudaError_t dispatch_word(int, int, bool, int, const LaunchParams*, int, size_t, cudaStream_t,
+                          int*);
+
+static cudaError_t dispatch(int fmt, int outk, bool wide, int cfg, const LaunchParams* p,
+                            int grid, size_t smem, cudaStream_t st, int* occ) {
+  switch (fmt) {
+    case FMT_NIB: return dispatch_nib(outk, wide, cfg, p, grid, smem, st, occ);
+    case FMT_BYTE: return dispatch_byte(outk, wide, cfg, p, grid, smem, st, occ);
+    case FMT_HALF: return dispatch_half(outk, wide, cfg, p, grid, smem, st, occ);
+    default: return dispatch_word(fmt, outk, wide, cfg, p, grid, smem, st, occ);
+  }
+}
+
+cudaError_t launch_dedisp(int fmt, int outk, bool wide, int cfg, const LaunchParams& p,
+                          int grid, size_t smem, cudaStream_t st) {
+  return dispatch(fmt, outk, wide, cfg, &p, grid, smem, st, nullptr);
+}
+
+cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, size_t smem,
+                                     int* nblk) {
+  *nblk = 0;
+  return dispatch(fmt, outk, wide, cfg, nullptr, 0, smem, nullptr, nblk);
+}
+
+size_t dedisp_smem_bytes(int fmt, int cfg, int cc, int nww) {
+  const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
+  return 4u * ((size_t)cc * fmt_spw(fmt) * nww + (size_t)B * cc);
+}
+
+// ---------------------------------------------------------------------------
+// Corner turn.  The paper transposes the input to frequency-major order by
+// whole words before dedispersing (Sec. 2.3); here one pass unpacks the
+// time-major 1/2/4/8-bit or float filterbank into per-channel image rows in
+// the staged lane format, zeroes killed channels (the arithmetic kill mask
+// of Sec. 2.3) and zero-pads outside [0, nrows_valid).
+//
+// Block = 256 threads over CB channels x WB image words.  Phase 1 reads the
+// raw rows of the block (32 bytes per row for packed input, 128 for float)
+// into shared memory with coalesced byte loads; phase 2 builds image words,
+// consecutive threads writing consecutive words of one channel row.
+// ---------------------------------------------------------------------------
+template <int NBITS>
+__global__ void __launch_bounds__(256) k_corner_turn(const uint8_t* __restrict__ in,
+                                                     int64_t in_stride, int64_t t_begin,
+                                                     int64_t nrows_valid, int nchans,
+                                                     const uint8_t* __restrict__ mask,
+                                                     uint32_t* __restrict__ img,
+                                                     int64_t row_words, int64_t words) {
+  constexpr bool F32 = (NBITS == 32);
+  constexpr int SPW = F32 ? 1 : (NBITS <= 2 ? 8 : (NBITS == 4 ? 4 : 2));
+  constexpr int LW = 32 / SPW;
+  constexpr int ROWB = F32 ? 128 : 32;           // raw bytes per row in the block
+  constexpr int CB = F32 ? 32 : 256 / NBITS;     // channels per block
+  constexpr int WB = F32 ? 64 : 32;              // image words per block
+  constexpr int R = WB * SPW;                    // raw rows per block
+  constexpr int PITCH = ROWB + 4;
+  __shared__ uint8_t tile[R * PITCH];
+
+  const int64_t w0 = (int64_t)blockIdx.x * WB;
+  const int cb0 = blockIdx.y * CB;
+  const int64_t rbytes = F32 ? (int64_t)nchans * 4 : ((int64_t)nchans * NBITS + 7) / 8;
+  const int64_t b0 = F32 ? (int64_t)cb0 * 4 : (int64_t)cb0 * NBITS / 8;
+  // raw row of image sample s: t_begin + s - kPad
+  const int64_t r0 = t_begin + w0 * SPW - kPad;
+
+  for (int e = threadIdx.x; e < R * ROWB; e += 256) {
+    const int rr = e / ROWB;
+    const int bb = e - rr * ROWB;
+    const int64_t r = r0 + rr;
+    const int64_t byte = b0 + bb;
+    uint8_t v = 0;
+    if (r >= t_begin && r < t_begin + nrows_valid && byte < rbytes) v = in[r * in_stride + byte];
+    tile[rr * PITCH + bb] = v;
+  }
+  __syncthreads();
+
+  for (int e = threadIdx.x; e < CB * WB; e += 256) {
+    const int cl = e / WB;
+    const int wl = e - cl * WB;
+    const int c = cb0 + cl;
+    const int64_t w = w0 + wl;
+    if (c >= nchans || w >= words) continue;
+    uint32_t word = 0;
+    if (F32) {
+      const int rr = wl;
+      word = *reinterpret_cast<const uint32_t*>(&tile[rr * PITCH + cl * 4]);
+    } else {
+      const int bitpos = cl * NBITS;
+#pragma unroll
+      for (int i = 0; i < SPW; ++i) {
+        const int rr = wl * SPW + i;
+        const uint32_t byte = tile[rr * PITCH + (bitpos >> 3)];
+        const uint32_t v = (byte >> (bitpos & 7)) & ((1u << NBITS) - 1u);
+        word |= v << (i * LW);
+      }
+    }
+    if (mask && mask[c] == 0) word = 0;
+    img[(int64_t)c * row_words + w] = word;
+  }
+}
+
+cudaError_t launch_corner_turn(int nbits, const uint8_t* in, int64_t in_stride, int64_t t_begin,
+                               int64_t nrows_valid, int nchans, const uint8_t* mask,
+                               uint32_t* img, int64_t row_words, int64_t words,
+                               cudaStream_t st) {
+  const int CB = nbits == 32 ? 32 : 256 / nbits;
+  const int WB = nbits == 32 ? 64 : 32;
+  dim3 grid((unsigned)((words + WB - 1) / WB), (unsigned)((nchans + CB - 1) / CB));
+  if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  switch (nbits) {
+    case 1: k_corner_turn<1><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, words); break;
+    case 2: k_corner_turn<2><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, words); break;
+    case 4: k_corner_turn<4><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, words); break;
+    case 8: k_corner_turn<8><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, words); break;
+    case 32: k_corner_turn<32><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, words); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Integer-add probe: each thread runs 8 independent chains of 32-bit adds of
+// run-time operands (one PTX add.u32 per counted add).  The result is stored
+// so nothing is dead.  Used as the compute roof of the roofline.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_probe_int_add(const uint32_t* __restrict__ seed,
+                                                       int64_t iters,
+                                                       uint32_t* __restrict__ sink) {
+  uint32_t a[8], b[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    a[k] = seed[k] ^ threadIdx.x;
+    b[k] = seed[8 + k] + blockIdx.x;
+  }
+  for (int64_t it = 0; it < iters; it += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) asm volatile("add.u32 %0, %0, %1;" : "+r"(a[k]) : "r"(b[k]));
+    }
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s ^= a[k];
+  sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t launch_probe(const uint32_t* seed, int64_t iters, uint32_t* sink, int grid,
+                         cudaStream_t st) {
+  k_probe_int_add<<<grid, 256, 0, st>>>(seed, iters, sink);
+  return cudaGetLastError();
+}
+
+}  // namespace dd

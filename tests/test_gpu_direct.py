@@ -1,0 +1,190 @@
+"""GPU parity of the direct transform (Eq. 2) against the CPU oracle.
+
+Integer input must match bit for bit; float input within |gpu - oracle| <=
+1e-5 * sum_c |A| (the FP64 oracle also returns sum_c |A|)."""
+import numpy as np
+import pytest
+
+import paper_1201_5380_gb300 as dd
+import synth
+from synth import configs
+from _gpu import odelays, run_direct, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-5
+
+
+def _survey_plan(hi=1000.0, step=1, **kw):
+    c = configs.SURVEY
+    full = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=hi))
+    dms = full.dms[::step]
+    return dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dms=dms, **kw)
+
+
+def test_tiny_config_bit_exact(orc):
+    c = configs.TINY
+    dms = configs.linear_dms(c["dms"])
+    plan = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dms=dms)
+    delays = odelays(orc, plan)
+    rows = c["nsamps"] + plan.max_delay
+    x = synth.normal_u8(c["seed"], 0, rows, c["nchans"])
+    p = c["pulses"][0]
+    x = synth.inject_boxcar(x, delays[p["dm_index"]], p["t0"], p["width"], amp=p["amp"])
+    got, _ = run_direct(plan, x, 8, c["nsamps"])
+    ref = orc.direct(x, 8, c["nchans"], c["nsamps"], delays)
+    assert np.array_equal(got, ref)
+    d, t = np.unravel_index(np.argmax(got), got.shape)
+    assert abs(int(d) - p["dm_index"]) <= 1
+
+
+def test_survey_band_subset_bit_exact(orc):
+    # 100 trials spread over 0..1000 (every 12th of the rule's list, so the
+    # high-DM blocks with wide staging windows are included), a ragged tail
+    plan = _survey_plan(step=12)
+    nsamps = 3000
+    rows = nsamps + plan.max_delay
+    x = synth.uniform_packed(2, 0, rows, 1024, 2)
+    got, _ = run_direct(plan, x, 2, nsamps)
+    assert np.array_equal(got, orc.direct(x, 2, 1024, nsamps, odelays(orc, plan)))
+
+
+@pytest.mark.parametrize("nbits", [1, 4, 8])
+def test_integer_formats_bit_exact(orc, nbits):
+    plan = _survey_plan(hi=2000.0, step=24)
+    nsamps = 2500
+    rows = nsamps + plan.max_delay
+    x = synth.uniform_packed(3, nbits, rows, 1024, nbits)
+    got, _ = run_direct(plan, x, nbits, nsamps)
+    assert np.array_equal(got, orc.direct(x, nbits, 1024, nsamps, odelays(orc, plan)))
+
+
+def test_float_input_within_tolerance(orc):
+    plan = _survey_plan(hi=2000.0, step=30)
+    nsamps = 1500
+    rows = nsamps + plan.max_delay
+    x = synth.normal_f32(4, 0, rows, 1024)
+    got, _ = run_direct(plan, x, 32, nsamps)
+    ref, ab = orc.direct_f32(x, nsamps, odelays(orc, plan))
+    err = np.abs(got.astype(np.float64) - ref)
+    assert np.all(err <= F32_TOL * ab), float((err / ab).max())
+
+
+def test_killmask_bit_exact(orc):
+    plan = _survey_plan(step=40)
+    mask = np.ones(1024, np.uint8)
+    mask[[0, 1, 2, 100, 511, 512, 1000, 1023]] = 0
+    mask[300:340] = 0
+    plan.set_killmask(mask)
+    nsamps = 2000
+    rows = nsamps + plan.max_delay
+    x = synth.uniform_packed(5, 0, rows, 1024, 2)
+    got, _ = run_direct(plan, x, 2, nsamps)
+    assert np.array_equal(got, orc.direct(x, 2, 1024, nsamps, odelays(orc, plan), mask))
+
+
+@pytest.mark.parametrize("nchans,ndm,nsamps,nbits", [
+    (64, 1, 1, 8), (64, 3, 7, 2), (5, 9, 333, 2), (12, 40, 1025, 4), (4, 33, 2049, 1),
+    (40, 17, 4097, 8), (300, 65, 999, 2)])
+def test_edge_shapes_bit_exact(orc, nchans, ndm, nsamps, nbits):
+    dms = np.linspace(0.0, 300.0, ndm) if ndm > 1 else np.array([77.0])
+    plan = dd.Plan(nchans, 64e-6, 1500.0, -200.0 / nchans, dms=dms)
+    rows = nsamps + plan.max_delay
+    x = synth.uniform_packed(6, nchans, rows, nchans, nbits)
+    got, _ = run_direct(plan, x, nbits, nsamps)
+    assert np.array_equal(got, orc.direct(x, nbits, nchans, nsamps, odelays(orc, plan)))
+
+
+def test_zero_dm_list_is_channel_sum(orc):
+    plan = dd.Plan(256, 64e-6, 1500.0, -0.5, dms=np.zeros(20))
+    nsamps = 1000
+    s = synth.uniform_samples(7, 0, nsamps, 256, 8)
+    got, _ = run_direct(plan, s, 8, nsamps)
+    assert np.array_equal(got, np.repeat(s.astype(np.uint32).sum(axis=1)[None, :], 20, axis=0))
+
+
+def test_unaligned_output_stride_and_rows(orc):
+    plan = _survey_plan(step=60)
+    nsamps = 1111
+    rows = nsamps + plan.max_delay
+    x = synth.uniform_packed(8, 0, rows, 1024, 2)
+    got, full = run_direct(plan, x, 2, nsamps, out_stride=nsamps + 3)
+    assert np.array_equal(got, orc.direct(x, 2, 1024, nsamps, odelays(orc, plan)))
+    # the padding past nsamps is untouched
+    assert np.all(full[:, nsamps:].view(np.int32) == -7)
+
+
+def test_host_pointer_path(orc):
+    plan = _survey_plan(step=50)
+    nsamps = 1500
+    rows = nsamps + plan.max_delay
+    x = synth.uniform_packed(9, 0, rows, 1024, 2)
+    out = np.zeros((plan.dm_count, nsamps), np.uint32)
+    plan.execute(x, 2, nsamps, out)
+    assert np.array_equal(out, orc.direct(x, 2, 1024, nsamps, odelays(orc, plan)))
+
+
+@pytest.mark.parametrize("tiling", [(32, 4, 4), (32, 8, 4), (32, 16, 4), (64, 8, 2), (64, 16, 2),
+                                    (16, 4, 4), (16, 8, 4)])
+def test_every_tiling_bit_exact(orc, tiling):
+    plan = _survey_plan(step=10)
+    plan.set_tuning(*tiling)
+    nsamps = 2100
+    rows = nsamps + plan.max_delay
+    x = synth.uniform_packed(10, 0, rows, 1024, 2)
+    got, _ = run_direct(plan, x, 2, nsamps)
+    assert np.array_equal(got, orc.direct(x, 2, 1024, nsamps, odelays(orc, plan)))
+
+
+def test_survey_full_size_sampled(orc):
+    """Config at full size (1024 ch, 2-bit, 1196 trials, 2^19 samples), in the
+    launch configuration the benchmark times; sampled points + the pulses."""
+    torch = torch_cuda()
+    c = configs.SURVEY
+    plan = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
+    assert plan.dm_count == 1196
+    G = c["nsamps"]
+    rows = G + plan.max_delay
+    delays = odelays(orc, plan)
+    x = synth.uniform_packed(c["seed"], 0, rows, 1024, 2)
+    dms = plan.dms
+    pulse_idx = []
+    for p in c["pulses"]:
+        k = int(np.argmin(np.abs(dms - p["dm"])))
+        pulse_idx.append(k)
+        x = synth.inject_boxcar_packed(x, 2, 1024, delays[k], p["t0"], p["width"], p["value"])
+    d_in = torch.from_numpy(x).cuda()
+    out = torch.empty((plan.dm_count, G), dtype=torch.int32, device="cuda")
+    plan.execute(d_in, 2, G, out)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    rng = np.random.default_rng(11)
+    ds = rng.integers(0, plan.dm_count, 3000)
+    ts = rng.integers(0, G, 3000)
+    ds = np.concatenate([ds, np.arange(plan.dm_count), np.full(8, plan.dm_count - 1)])
+    ts = np.concatenate([ts, np.full(plan.dm_count, G - 1), np.arange(G - 8, G)])
+    for k, p in zip(pulse_idx, c["pulses"]):
+        ds = np.concatenate([ds, np.full(p["width"], k)])
+        ts = np.concatenate([ts, p["t0"] + np.arange(p["width"])])
+    got = out[torch.from_numpy(ds).cuda(), torch.from_numpy(ts).cuda()].cpu().numpy().view(np.uint32)
+    ref = orc.direct_points(x, 2, 1024, delays, ds, ts)
+    assert np.array_equal(got, ref)
+    for k, p in zip(pulse_idx, c["pulses"]):
+        seg = out[k, p["t0"]:p["t0"] + p["width"]].cpu().numpy()
+        assert np.all(seg == 3 * 1024)
+
+
+def test_autotune_keeps_results_exact(orc):
+    plan = _survey_plan(step=20)
+    plan.autotune(2, 8192)
+    nsamps = 1700
+    rows = nsamps + plan.max_delay
+    x = synth.uniform_packed(12, 0, rows, 1024, 2)
+    got, _ = run_direct(plan, x, 2, nsamps)
+    assert np.array_equal(got, orc.direct(x, 2, 1024, nsamps, odelays(orc, plan)))
+
+
+def test_integer_add_probe_runs():
+    torch_cuda()
+    rate, ms = dd.probe_int_add(1 << 14)
+    assert rate > 1e12 and ms > 0

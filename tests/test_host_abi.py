@@ -1,0 +1,124 @@
+"""CPU-only checks of the C ABI: the library loads and exports every call
+declared in include/*.h, and the host-side plan logic (trial-DM rule, delay
+table of Eq. 3-4, sub-band tables, validation) agrees with the oracle."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1201_5380_gb300 as dd
+from synth import configs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+char\s*\*|void|dd_status)\s*\*?\s*(dd_\w+)\s*\(",
+                             text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_call():
+    names = _declared_symbols()
+    assert len(names) >= 30
+    lib = ctypes.CDLL(dd.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings():
+    lib = dd.lib()
+    for code in range(12):
+        assert lib.dd_status_string(code)
+
+
+BANDS = [
+    (configs.SURVEY, 0.0, 1000.0),
+    (configs.FORMAT_SWEEP, 0.0, 2000.0),
+    (dict(nchans=512, f0=1581.8, df=-0.78125, dt=64e-6), 0.0, 2000.0),
+]
+
+
+@pytest.mark.parametrize("band,lo,hi", BANDS)
+def test_dm_list_and_delays_match_oracle(orc, band, lo, hi):
+    p = dd.Plan(band["nchans"], band["dt"], band["f0"], band["df"],
+                dm_rule=dict(lo=lo, hi=hi, width_us=40.0, tol=1.25))
+    ref = orc.dm_list(band["nchans"], band["f0"], band["df"], band["dt"], lo, hi)
+    assert np.array_equal(p.dms, ref)
+    tab = orc.delay_table(band["nchans"], band["f0"], band["df"], band["dt"], p.dms)
+    assert np.array_equal(p.delay_table(), tab)
+    assert p.max_delay == int(tab.max())
+
+
+def test_survey_dm_count_is_the_papers():
+    c = configs.SURVEY
+    p = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
+    assert p.dm_count == 1196
+
+
+def test_user_dm_list_delays_match_oracle(orc):
+    c = configs.TINY
+    dms = configs.linear_dms(c["dms"])
+    p = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dms=dms)
+    assert np.array_equal(p.delay_table(),
+                          orc.delay_table(c["nchans"], c["f0"], c["df"], c["dt"], dms))
+
+
+@pytest.mark.parametrize("nsub,ndmn", [(32, 32), (16, 8), (1, 4), (8, 1)])
+def test_subband_max_delay_matches_oracle(orc, nsub, ndmn):
+    c = configs.SURVEY
+    p = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0),
+                subband=(nsub, ndmn))
+    assert p.subband_max_delay == orc.subband_max_delay(p.delay_table(), nsub, ndmn)
+
+
+def test_plan_validation():
+    with pytest.raises(dd.DedispError):
+        dd.Plan(0, 64e-6, 1500.0, -1.0)
+    with pytest.raises(dd.DedispError):
+        dd.Plan(64, 64e-6, 1500.0, +1.0)           # ascending band
+    with pytest.raises(dd.DedispError):
+        dd.Plan(64, 64e-6, 50.0, -1.0)             # last channel below 0 MHz
+    with pytest.raises(dd.DedispError):
+        dd.Plan(64, -1.0, 1500.0, -1.0)
+    p = dd.Plan(64, 64e-6, 1500.0, -1.0)
+    with pytest.raises(dd.DedispError):
+        p.set_dm_list([0.0, 2.0, 1.0])             # decreasing
+    with pytest.raises(dd.DedispError):
+        p.set_dm_list([-1.0])
+    with pytest.raises(dd.DedispError):
+        p.dms                                      # no DM list yet
+    with pytest.raises(dd.DedispError):
+        p.set_subband(5, 4)                        # 5 does not divide 64
+    p.set_dm_list([0.0, 1.0])
+    assert p.dm_count == 2
+
+
+def test_tuning_api():
+    p = dd.Plan(64, 64e-6, 1500.0, -1.0, dms=[0.0, 1.0])
+    p.set_tuning(64, 16, 2)
+    assert p.get_tuning() == dict(dms_per_block=64, chans_per_chunk=16, words_per_lane=2)
+    with pytest.raises(dd.DedispError):
+        p.set_tuning(48, 8, 4)
+    with pytest.raises(dd.DedispError):
+        p.set_tuning(32, 6, 4)
+
+
+def test_execute_rejects_bad_arguments_without_a_gpu():
+    p = dd.Plan(16, 64e-6, 1500.0, -1.0, dms=[0.0, 5.0])
+    a = np.zeros((100, 16), np.uint8)
+    o = np.zeros((2, 10), np.uint32)
+    with pytest.raises(dd.DedispError) as e:
+        p.execute(a, 3, 10, o)
+    assert e.value.code == 3
+    with pytest.raises(dd.DedispError) as e:
+        p.execute(a, 8, 20, o)                     # output row shorter than nsamps
+    assert e.value.code == 1
