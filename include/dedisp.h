@@ -129,7 +129,7 @@ dd_status dd_plan_set_subband(dd_plan plan, int chans_per_subband,
                               int dms_per_nominal);
 
 /* Kernel tiling: trials per thread block (16, 32 or 64), channels staged
- * per pass (multiple of 4, <= 32) and output words per lane (2 or 4);
+ * per pass (4, 8, 16 or 32) and output words per lane (2 or 4);
  * 0 selects the built-in default for each.  The autotuner below sets these. */
 dd_status dd_plan_set_tuning(dd_plan plan, int dms_per_block, int chans_per_chunk,
                              int words_per_lane);

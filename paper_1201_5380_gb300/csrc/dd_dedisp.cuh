@@ -208,6 +208,78 @@ __device__ __forceinline__ int find_seg(const LaunchParams& p, int64_t item) {
   return lo;
 }
 
+// ---------------------------------------------------------------------------
+// TMA (bulk async copy) and mbarrier helpers.  Every wait is bounded: after
+// kWaitLimit polls the kernel records DEV_TIMEOUT and carries on, so a lost
+// transfer can never hang the GPU.
+// ---------------------------------------------------------------------------
+constexpr int kWaitLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completion counted in bytes on `bar`.
+__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void* src, uint32_t bytes,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
+// Window start (image word, multiple of 4) of a channel whose first trial
+// has delay s0, for a tile starting at output time t0.
+template <int SPW>
+__device__ __forceinline__ int64_t window_word(int64_t t0, int32_t s0, int lo_slack) {
+  const int64_t b = t0 + kPad + (int64_t)s0 - lo_slack;  // >= 0 (kPad >= lo_slack)
+  return (b / (4 * SPW)) * 4;
+}
+
+// Shared-memory layout (32-bit words), two buffers of each region:
+//   [0,4)            two mbarriers
+//   landing[2][cc][nww+4]          TMA destination: raw image window
+//   copies [2][cc*SPW][nww]        SPW lane-shifted copies of each window
+//   addr   [2][B*cc]               byte address of each (trial, channel)
+//                                  window inside copies (lane 0, word 0)
+//
+// Per chunk (cc channels) of an item, one __syncthreads:
+//   prefetch next chunk's delays -> registers
+//   wait for this chunk's TMA; build its shifted copies from the landing area
+//   __syncthreads
+//   warp 0 issues the next chunk's TMA; all threads write its address table
+//   shift-and-sum this chunk
 template <int FMT, int OUTK, bool WIDE, int NWARP, int DPW, int K>
 __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(const LaunchParams p) {
   constexpr int SPW = FmtT<FMT>::SPW;
@@ -217,14 +289,35 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
   constexpr int T = 32 * K * SPW;
 
   extern __shared__ uint4 smem4[];
-  uint32_t* s_copy = reinterpret_cast<uint32_t*>(smem4);
-  const int cc = p.cc;
+  uint32_t* const sm = reinterpret_cast<uint32_t*>(smem4);
+  const int cc = p.cc;              // power of two, 4..32
+  const int cc_log = 31 - __clz(cc);
   const int nww = p.nww;
-  uint32_t* s_addr = s_copy + (size_t)cc * SPW * nww;
+  const int nwl = nww + 4;
+  const uint32_t sm_base = smem_addr(sm);
+  const uint32_t bar0 = sm_base;    // two 8-byte mbarriers at word 0 and 2
+  // one sample per word needs no shifted copies: lanes read the landing area
+  constexpr bool COPIES = SPW > 1;
+  uint32_t* const landing = sm + 4;
+  uint32_t* const copies = landing + 2 * cc * nwl;
+  const int landing_words = cc * nwl;
+  const int copy_words = COPIES ? cc * SPW * nww : 0;
+  uint32_t* const s_addr = copies + 2 * copy_words;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
+  // address-table entries of this thread: e = tid + r*NT, e < B*cc (r < 2)
+  const int n_entries = B << cc_log;
+
+  if (tid == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar0 + 8, 1);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+
+  uint32_t kk = 0;  // chunks consumed by this block (buffer = kk & 1, parity = (kk >> 1) & 1)
 
   for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
     const Seg& S = p.segs[find_seg(p, item)];
@@ -235,9 +328,17 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
     const int64_t rem = li - tile * per_tile;
     const int grp = (int)(rem / n_dmblk);
     const int blk = (int)(rem - (int64_t)grp * n_dmblk);
-    const int d0 = blk * B;
     const int ndm_g = (grp == S.n_groups - 1) ? S.ndm_last : S.ndm;
-    const int nd = min(B, ndm_g - d0);
+    int d0, nd;
+    if (S.blk) {
+      const int32_t* bt = S.blk + (int64_t)grp * (n_dmblk + 1);
+      d0 = __ldg(&bt[blk]);
+      nd = min(B, __ldg(&bt[blk + 1]) - d0);
+      if (nd == 0) continue;  // padding block of a group with fewer blocks
+    } else {
+      d0 = blk * B;
+      nd = min(B, ndm_g - d0);
+    }
     const int64_t t0 = tile * T;
     const int64_t t_end = min(t0 + T, S.nsamps);
     const int nchan = S.nchan;
@@ -251,6 +352,74 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       if (tid == 0) atomicOr(p.status, DEV_BAD_ITEM);
       continue;
     }
+    const int nchunks = (nchan + cc - 1) >> cc_log;
+
+    // Delays of this thread's address-table entries for chunk c0:
+    // entry e -> (slot = e >> cc_log, channel c = e & (cc-1)); s0 = first trial.
+    int32_t pf_s[2], pf_s0[2];
+    auto prefetch = [&](int c0) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int e = tid + r * NT;
+        pf_s[r] = pf_s0[r] = 0;
+        if (e < n_entries) {
+          const int slot = e >> cc_log;
+          const int cabs = min(c0 + (e & (cc - 1)), nchan - 1);
+          const int d = d0 + min(slot, nd - 1);
+          pf_s0[r] = __ldg(&delays[(int64_t)d0 * dstride + cabs]);
+          pf_s[r] = __ldg(&delays[(int64_t)d * dstride + cabs]);
+        }
+      }
+    };
+    // Address table and TMA of chunk c0 into buffer nb (uses the prefetch).
+    auto issue = [&](int c0, int nb) {
+      uint32_t* const sa = s_addr + nb * n_entries;
+      const uint32_t copies_b = smem_addr(copies + nb * copy_words);
+      const uint32_t land_b = smem_addr(landing + nb * landing_words);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int e = tid + r * NT;
+        if (e < n_entries) {
+          const int c = e & (cc - 1);
+          // zero window (c >= nchan): the build step clears it
+          uint32_t a = COPIES ? copies_b + (uint32_t)(c * SPW * nww) * 4u
+                              : land_b + (uint32_t)(c * nwl) * 4u;
+          if (c0 + c < nchan) {
+            const int64_t base = window_word<SPW>(t0, pf_s0[r], lo_slack) * SPW;
+            const int64_t o = t0 + kPad + (int64_t)pf_s[r] - base;
+            const int kap = (int)(o & (SPW - 1));
+            int64_t om = o / SPW;
+            if (o < 0 || om + 32 * K > nww) {
+              atomicOr(p.status, DEV_BAD_WINDOW);
+              om = 0;
+            }
+            a = COPIES ? copies_b + ((uint32_t)((c * SPW + kap) * nww) + (uint32_t)om) * 4u
+                       : land_b + ((uint32_t)(c * nwl) + (uint32_t)om) * 4u;
+          }
+          sa[e] = a;
+        }
+      }
+      if (warp == 0) {
+        // Window of channel c0+lane; a window running past the end of its
+        // row (a launch over images of different lengths) is shortened: the
+        // words past the row are beyond every valid output of this image.
+        const uint32_t bar = bar0 + 8u * nb;
+        const int cabs = min(c0 + lane, nchan - 1);
+        int64_t wi = window_word<SPW>(t0, pf_s0[0], lo_slack);
+        if (lane < cc && (wi < 0 || wi + 4 > row_words)) {
+          atomicOr(p.status, DEV_BAD_READ);
+          wi = 0;
+        }
+        const uint32_t words = (uint32_t)min((int64_t)nwl, row_words - wi);
+        const uint32_t total = __reduce_add_sync(0xffffffffu, lane < cc ? words * 4u : 0u);
+        if (lane == 0) mbar_arrive_expect_tx(bar, total);
+        if (lane < cc) {
+          fence_proxy_async_smem();
+          tma_load_1d(smem_addr(landing + nb * landing_words + lane * nwl),
+                      img + (int64_t)cabs * row_words + wi, words * 4u, bar);
+        }
+      }
+    };
 
     Acc<FMT, WIDE> acc[DPW][K];
 #pragma unroll
@@ -259,51 +428,41 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       for (int j = 0; j < K; ++j) acc[i][j].zero();
     int g0 = 0, g1 = 0, g2 = 0;
 
-    for (int c0 = 0; c0 < nchan; c0 += cc) {
-      // (a) word address of each (trial slot, channel) window in the copies
-      for (int e = tid; e < B * cc; e += NT) {
-        const int slot = e / cc;
-        const int c = e - slot * cc;
-        const int cabs = c0 + c;
-        uint32_t a = (uint32_t)(c * SPW) * (uint32_t)nww;
-        if (cabs < nchan) {
-          const int d = d0 + min(slot, nd - 1);
-          const int64_t s0 = __ldg(&delays[(int64_t)d0 * dstride + cabs]);
-          const int64_t s = __ldg(&delays[(int64_t)d * dstride + cabs]);
-          const int64_t base = ((t0 + kPad + s0 - lo_slack) / (4 * SPW)) * (4 * SPW);
-          const int64_t o = t0 + kPad + s - base;
-          const int kap = (int)(o % SPW);
-          int64_t om = o / SPW;
-          if (o < 0 || om + 32 * K > nww) {
-            atomicOr(p.status, DEV_BAD_WINDOW);
-            om = 0;
-          }
-          a = (uint32_t)(c * SPW + kap) * (uint32_t)nww + (uint32_t)om;
-        }
-        s_addr[e] = a;
+    // prologue: chunk 0
+    prefetch(0);
+    issue(0, kk & 1);
+
+    for (int k = 0; k < nchunks; ++k, ++kk) {
+      const int buf = kk & 1;
+      const int c0 = k << cc_log;
+      const bool more = k + 1 < nchunks;
+      if (more) prefetch(c0 + cc);
+      // (a) wait for the chunk's windows, then build the SPW shifted copies
+      if (!mbar_wait_bounded(bar0 + 8u * buf, (kk >> 1) & 1u)) {
+        atomicOr(p.status, DEV_TIMEOUT);
+        mbar_wait_bounded(bar0 + 8u * buf, (kk >> 1) & 1u);
       }
-      // (b) stage the chunk: SPW lane-shifted copies of each channel window
-      {
+      if (!COPIES) {
+        if (c0 + cc > nchan) {
+          uint32_t* const land = landing + buf * landing_words;
+          for (int e = tid; e < (c0 + cc - nchan) * nwl; e += NT)
+            land[(nchan - c0) * nwl + e] = 0u;
+        }
+      } else {
+        const uint32_t* const land = landing + buf * landing_words;
+        uint32_t* const cp = copies + buf * copy_words;
+        const int tpc_log = (31 - __clz(NT)) - cc_log;  // threads per channel = NT / cc
+        const int c = tid >> tpc_log;
         const int nq = nww >> 2;
-        for (int e = tid; e < cc * nq; e += NT) {
-          const int c = e / nq;
-          const int q = e - c * nq;
-          const int cabs = c0 + c;
+        const bool live = c0 + c < nchan;
+        for (int q = tid & ((1 << tpc_log) - 1); q < nq; q += (1 << tpc_log)) {
           uint4 w = make_uint4(0u, 0u, 0u, 0u);
           uint32_t w4 = 0u;
-          if (cabs < nchan) {
-            const int64_t s0 = __ldg(&delays[(int64_t)d0 * dstride + cabs]);
-            const int64_t base = ((t0 + kPad + s0 - lo_slack) / (4 * SPW)) * (4 * SPW);
-            const int64_t wi = base / SPW + 4 * q;
-            const uint32_t* row = img + (int64_t)cabs * row_words;
-            if (wi >= 0 && wi + 4 < row_words) {
-              w = __ldg(reinterpret_cast<const uint4*>(row + wi));
-              w4 = __ldg(row + wi + 4);
-            } else {
-              atomicOr(p.status, DEV_BAD_READ);
-            }
+          if (live) {
+            w = *reinterpret_cast<const uint4*>(land + c * nwl + 4 * q);
+            w4 = land[c * nwl + 4 * q + 4];
           }
-          uint32_t* dst = s_copy + (size_t)(c * SPW) * nww + 4 * q;
+          uint32_t* dst = cp + c * SPW * nww + 4 * q;
 #pragma unroll
           for (int kap = 0; kap < SPW; ++kap) {
             uint4 v;
@@ -315,23 +474,27 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
               v.z = __funnelshift_r(w.z, w.w, kap * LW);
               v.w = __funnelshift_r(w.w, w4, kap * LW);
             }
-            *reinterpret_cast<uint4*>(dst + (size_t)kap * nww) = v;
+            *reinterpret_cast<uint4*>(dst + kap * nww) = v;
           }
         }
       }
       __syncthreads();
+      // (b) next chunk's address table and TMA (its buffers were released by
+      //     the barrier above)
+      if (more) issue(c0 + cc, buf ^ 1);
       // (c) shift-and-sum over the chunk, four channels per group
+      const uint32_t* const sa = s_addr + buf * n_entries;
+      const uint32_t lane_off = (uint32_t)lane * 4u;
       for (int cg = 0; cg < cc; cg += 4) {
 #pragma unroll
         for (int i = 0; i < DPW; ++i) {
-          const uint4 a4 = *reinterpret_cast<const uint4*>(s_addr + (warp * DPW + i) * cc + cg);
-          const uint32_t* q0 = s_copy + a4.x + lane;
-          const uint32_t* q1 = s_copy + a4.y + lane;
-          const uint32_t* q2 = s_copy + a4.z + lane;
-          const uint32_t* q3 = s_copy + a4.w + lane;
+          const uint4 a4 = *reinterpret_cast<const uint4*>(sa + ((warp * DPW + i) << cc_log) + cg);
+          const uint32_t q0 = a4.x + lane_off, q1 = a4.y + lane_off;
+          const uint32_t q2 = a4.z + lane_off, q3 = a4.w + lane_off;
 #pragma unroll
           for (int j = 0; j < K; ++j)
-            acc[i][j].add4(q0[32 * j], q1[32 * j], q2[32 * j], q3[32 * j]);
+            acc[i][j].add4(lds32(q0 + 128u * j), lds32(q1 + 128u * j), lds32(q2 + 128u * j),
+                           lds32(q3 + 128u * j));
         }
         if (++g0 == p.f0) {
           g0 = 0;
@@ -355,8 +518,9 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
           }
         }
       }
-      __syncthreads();
     }
+    // all warps are done with this item's buffers before the next prologue
+    __syncthreads();
 
     // (d) exact sums out: u32 rows, float rows, or 16-bit image rows
 #pragma unroll

@@ -48,6 +48,43 @@ int32_t max_block_spread(const int32_t* delays, int ndm, int nchans, int stride,
   return spread + lo;
 }
 
+void make_blocks(const int32_t* delays, int ndm, int nchans, int stride, int B, int32_t budget,
+                 std::vector<int32_t>* starts, int32_t* spread_out, int32_t* lo_out) {
+  starts->clear();
+  int32_t spread_all = 0, lo_all = 0;
+  std::vector<int32_t> mn(nchans), mx(nchans);
+  int d0 = 0;
+  while (d0 < ndm) {
+    starts->push_back(d0);
+    const int32_t* r0 = delays + (size_t)d0 * stride;
+    for (int c = 0; c < nchans; ++c) mn[c] = mx[c] = r0[c];
+    int32_t sp = 0, lo = 0;
+    int d = d0 + 1;
+    for (; d < ndm && d < d0 + B; ++d) {
+      const int32_t* r = delays + (size_t)d * stride;
+      int32_t sp2 = 0, lo2 = 0;
+      for (int c = 0; c < nchans; ++c) {
+        const int32_t a = std::min(mn[c], r[c]), b = std::max(mx[c], r[c]);
+        lo2 = std::max(lo2, r0[c] - a);
+        sp2 = std::max(sp2, b - r0[c]);
+      }
+      if (sp2 + lo2 > budget) break;
+      for (int c = 0; c < nchans; ++c) {
+        mn[c] = std::min(mn[c], r[c]);
+        mx[c] = std::max(mx[c], r[c]);
+      }
+      sp = sp2;
+      lo = lo2;
+    }
+    spread_all = std::max(spread_all, sp + lo);
+    lo_all = std::max(lo_all, lo);
+    d0 = d;
+  }
+  starts->push_back(ndm);
+  *spread_out = spread_all;
+  *lo_out = lo_all;
+}
+
 int time_tile(int fmt, const Tuning& t) { return 32 * t.words_per_lane * fmt_spw(fmt); }
 
 static int window_words(int fmt, const Tuning& t, int32_t spread) {
@@ -115,10 +152,15 @@ static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector
     nchan_max = std::max(nchan_max, (int)s.seg.nchan);
   }
   const int nww = window_words(fmt, p.tune, spread);
-  int cc = p.tune.chans_per_chunk;
+  // channels per chunk: a power of two, at most two address-table entries
+  // per thread, and both staging buffers within the shared-memory budget
+  const int nt = kTileCfgs[cfg].nwarp * 32;
+  int cc = 4;
+  while (cc * 2 <= p.tune.chans_per_chunk) cc *= 2;
   const size_t smem_cap = 220 * 1024;
-  while (cc > 4 && dedisp_smem_bytes(fmt, cfg, cc, nww) > smem_cap) cc -= 4;
-  if (dedisp_smem_bytes(fmt, cfg, cc, nww) > smem_cap) return DD_ERR_INVALID_ARG;
+  while (cc > 4 && (dedisp_smem_bytes(fmt, cfg, cc, nww) > smem_cap || B * cc > 2 * nt)) cc /= 2;
+  if (dedisp_smem_bytes(fmt, cfg, cc, nww) > smem_cap || B * cc > 2 * nt)
+    return DD_ERR_INVALID_ARG;
 
   L->fmt = fmt;
   L->outk = outk;
@@ -130,7 +172,7 @@ static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector
     if (g.n_groups < 1) g.n_groups = 1;
     if (g.ndm_last <= 0) g.ndm_last = g.ndm;
     if (g.ndm <= 0 || g.nsamps <= 0) continue;
-    g.n_dmblk = (g.ndm + B - 1) / B;
+    if (!g.blk) g.n_dmblk = (g.ndm + B - 1) / B;
     const int64_t tiles = (g.nsamps + T - 1) / T;
     g.item_begin = items;
     items += (int64_t)g.n_dmblk * g.n_groups * tiles;
@@ -183,6 +225,9 @@ dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
     const int bi = b_index(B);
     int32_t lo = j.plan->lo_B[bi];
     s.spread = j.plan->spread_B[bi];
+    s.seg.blk = static_cast<const int32_t*>(j.plan->d_blk[bi].p);
+    s.seg.n_dmblk = (int32_t)j.plan->blocks_B[bi].size() - 1;
+    if (!s.seg.blk) return DD_ERR_INVALID_ARG;
     s.seg.img = j.img;
     s.seg.delays = j.d_delays;
     s.seg.out = j.out;
@@ -352,6 +397,8 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
     g.g_delay = Np;
     g.g_out = rw2;
     g.lo_slack = lo1;
+    g.blk = static_cast<const int32_t*>(p.d_sb1_blk[bi].p);
+    g.n_dmblk = p.sb1_nblk_B[bi];
     g.nsamps = len1;
     g.out = S + (half ? kPad / 2 : kPad);
     g.out_stride = (int64_t)nsb * rw2;
@@ -380,6 +427,8 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
     q.g_delay = p.sb_dms * nsb;
     q.g_out = (int64_t)p.sb_dms * a.out_stride;
     q.lo_slack = lo2;
+    q.blk = static_cast<const int32_t*>(p.d_sb2_blk[bi].p);
+    q.n_dmblk = p.sb2_nblk_B[bi];
     q.nsamps = G;
     q.out = a.out;
     q.out_stride = a.out_stride;

@@ -46,6 +46,7 @@ enum : uint32_t {
   DEV_BAD_WINDOW = 1u,  // a lane window ran past the staged copy
   DEV_BAD_READ = 2u,    // staging read past an image row
   DEV_BAD_ITEM = 4u,    // malformed work item
+  DEV_TIMEOUT = 8u,     // a bounded wait for a bulk copy expired
 };
 
 // One regular grid of work: n_groups groups, each `ndm` trials (`ndm_last` in
@@ -54,6 +55,8 @@ enum : uint32_t {
 // sub-band stage 1, trial groups in stage 2; a direct job has one group).
 // Items of a segment are (time tile, group, trial block), trial block fastest.
 struct Seg {
+  const int32_t* blk;     // optional trial-block starts (n_dmblk + 1 entries,
+                          // device); null = regular blocks of B trials
   const uint32_t* img;    // image row of channel 0 (group 0)
   const int32_t* delays;  // delay of trial 0, channel 0 (group 0)
   void* out;              // output row of trial 0 at time 0 (group 0)
@@ -149,9 +152,16 @@ struct Plan {
   // staging spreads (incl. lo_slack) and lo_slack per trials-per-block
   // B = 16 << i, for the direct table and the two sub-band stages
   int32_t spread_B[3] = {0, 0, 0}, lo_B[3] = {0, 0, 0};
+  std::vector<int32_t> blocks_B[3];  // trial-block starts (+ end) per B
+  DevBuf d_blk[3];
+  bool blk_dirty = true;
   int32_t sb1_spread_B[3] = {0, 0, 0}, sb1_lo_B[3] = {0, 0, 0};
   int32_t sb2_spread_B[3] = {0, 0, 0}, sb2_lo_B[3] = {0, 0, 0};
   int32_t sb_maxrel = 0;
+  // per-group trial-block tables of the two sub-band stages, per B
+  std::vector<int32_t> sb1_blk_B[3], sb2_blk_B[3];
+  int32_t sb1_nblk_B[3] = {0, 0, 0}, sb2_nblk_B[3] = {0, 0, 0};
+  DevBuf d_sb1_blk[3], d_sb2_blk[3];
   // kernel timing (dd_plan_set_kernel_timing)
   bool timing = false;
   struct TimedLaunch {
@@ -227,6 +237,16 @@ int64_t image_row_words(int fmt, const Tuning& t, int64_t nsamps, int32_t maxd,
                         int32_t spread);
 int32_t max_block_spread(const int32_t* delays, int ndm, int nchans, int stride,
                          int B, int32_t* lo_slack);
+// Cut trials into blocks of at most B whose staging spread stays within
+// budget samples (a lone trial always forms a block); returns the block
+// starts plus the end, and the largest spread / lo_slack of the blocks.
+void make_blocks(const int32_t* delays, int ndm, int nchans, int stride, int B,
+                 int32_t budget, std::vector<int32_t>* starts, int32_t* spread,
+                 int32_t* lo_slack);
+// Largest staging spread (samples) of a trial block: with double-buffered
+// staging and 4-channel chunks the windows of every format then fit in
+// 220 KB of shared memory.
+constexpr int32_t kSpreadBudget = 4400;
 int time_tile(int fmt, const Tuning& t);
 dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
                              const std::vector<DirectJob>& jobs, LaunchPlan* lpl);

@@ -34,9 +34,12 @@ cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, size
   return dispatch(fmt, outk, wide, cfg, nullptr, 0, smem, nullptr, nblk);
 }
 
+// Two mbarriers, then two buffers each of: landing windows (cc x (nww+4)),
+// SPW shifted copies (cc x SPW x nww) and the address table (B x cc).
 size_t dedisp_smem_bytes(int fmt, int cfg, int cc, int nww) {
   const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
-  return 4u * ((size_t)cc * fmt_spw(fmt) * nww + (size_t)B * cc);
+  const size_t copies = fmt_spw(fmt) > 1 ? (size_t)cc * fmt_spw(fmt) * nww : 0;
+  return 16u + 4u * 2u * ((size_t)cc * (nww + 4) + copies + (size_t)B * cc);
 }
 
 // ---------------------------------------------------------------------------

@@ -103,7 +103,9 @@ static dd_status build_delays(Plan& p) {
   p.delays.swap(tab);
   p.max_delay = mx;
   for (int i = 0; i < 3; ++i)
-    p.spread_B[i] = max_block_spread(p.delays.data(), n, p.nchans, p.nchans, 16 << i, &p.lo_B[i]);
+    make_blocks(p.delays.data(), n, p.nchans, p.nchans, 16 << i, kSpreadBudget, &p.blocks_B[i],
+                &p.spread_B[i], &p.lo_B[i]);
+  p.blk_dirty = true;
   p.delays_dirty = true;
   p.sb_dirty = true;
   return DD_OK;
@@ -133,6 +135,16 @@ dd_status ensure_device_tables(Plan& p) {
         cudaSuccess)
       return cuda_status(e);
     p.mask_dirty = false;
+  }
+  if (p.blk_dirty) {
+    for (int i = 0; i < 3; ++i) {
+      const size_t nb = p.blocks_B[i].size() * sizeof(int32_t);
+      if ((e = p.d_blk[i].ensure(nb)) != cudaSuccess) return cuda_status(e);
+      if ((e = cudaMemcpy(p.d_blk[i].p, p.blocks_B[i].data(), nb, cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+        return cuda_status(e);
+    }
+    p.blk_dirty = false;
   }
   if (!p.d_status.p) {
     if ((e = p.d_status.ensure(sizeof(uint32_t))) != cudaSuccess) return cuda_status(e);
@@ -180,25 +192,54 @@ dd_status prepare_subband(Plan& p) {
   p.sb_len1_extra = m2;
   p.sb_maxrel = 0;
   for (int32_t v : p.sb_rel) p.sb_maxrel = std::max(p.sb_maxrel, v);
+  // Trial blocks of each group (sub-band in stage 1, trial group in stage
+  // 2), cut to the staging budget; groups with fewer blocks are padded with
+  // empty ones so the table is [groups][nblk + 1].
+  auto group_tables = [&](int ngrp, int B, auto rows_of, std::vector<int32_t>* table,
+                          int32_t* nblk, int32_t* spread, int32_t* lo) {
+    std::vector<std::vector<int32_t>> per(ngrp);
+    int32_t sp = 0, l = 0, mb = 0;
+    for (int g = 0; g < ngrp; ++g) {
+      const int32_t* rows;
+      int nrows, width, stride;
+      rows_of(g, &rows, &nrows, &width, &stride);
+      int32_t s1 = 0, l1 = 0;
+      make_blocks(rows, nrows, width, stride, B, kSpreadBudget, &per[g], &s1, &l1);
+      sp = std::max(sp, s1);
+      l = std::max(l, l1);
+      mb = std::max(mb, (int32_t)per[g].size() - 1);
+    }
+    table->assign((size_t)ngrp * (mb + 1), 0);
+    for (int g = 0; g < ngrp; ++g) {
+      const int nb = (int)per[g].size() - 1;
+      for (int b = 0; b <= mb; ++b)
+        (*table)[(size_t)g * (mb + 1) + b] = per[g][std::min(b, nb)];
+    }
+    *nblk = mb;
+    *spread = sp;
+    *lo = l;
+  };
   for (int i = 0; i < 3; ++i) {
     const int B = 16 << i;
-    int32_t sp1 = 0, lo1 = 0, sp2 = 0, lo2 = 0;
-    for (int s = 0; s < nsb; ++s) {
-      int32_t lo = 0;
-      sp1 = std::max(sp1, max_block_spread(p.sb_rel.data() + (size_t)s * Np, ng, Np, C, B, &lo));
-      lo1 = std::max(lo1, lo);
-    }
-    for (int g = 0; g < ng; ++g) {
-      const int d0 = g * p.sb_dms;
-      const int nd = std::min(p.sb_dms, n - d0);
-      int32_t lo = 0;
-      sp2 = std::max(sp2, max_block_spread(p.sb_d2.data() + (size_t)d0 * nsb, nd, nsb, nsb, B, &lo));
-      lo2 = std::max(lo2, lo);
-    }
-    p.sb1_spread_B[i] = sp1;
-    p.sb1_lo_B[i] = lo1;
-    p.sb2_spread_B[i] = sp2;
-    p.sb2_lo_B[i] = lo2;
+    group_tables(
+        nsb, B,
+        [&](int g, const int32_t** r, int* nr, int* w, int* st) {
+          *r = p.sb_rel.data() + (size_t)g * Np;
+          *nr = ng;
+          *w = Np;
+          *st = C;
+        },
+        &p.sb1_blk_B[i], &p.sb1_nblk_B[i], &p.sb1_spread_B[i], &p.sb1_lo_B[i]);
+    group_tables(
+        ng, B,
+        [&](int g, const int32_t** r, int* nr, int* w, int* st) {
+          const int d0 = g * p.sb_dms;
+          *r = p.sb_d2.data() + (size_t)d0 * nsb;
+          *nr = std::min(p.sb_dms, n - d0);
+          *w = nsb;
+          *st = nsb;
+        },
+        &p.sb2_blk_B[i], &p.sb2_nblk_B[i], &p.sb2_spread_B[i], &p.sb2_lo_B[i]);
   }
   p.sb_dirty = false;
   p.sb_dev_dirty = true;
@@ -219,6 +260,15 @@ dd_status upload_subband(Plan& p) {
   if ((e = cudaMemcpy(p.d_sb_d2.p, p.sb_d2.data(), p.sb_d2.size() * 4,
                       cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_status(e);
+  for (int i = 0; i < 3; ++i) {
+    if ((e = p.d_sb1_blk[i].ensure(p.sb1_blk_B[i].size() * 4)) != cudaSuccess ||
+        (e = cudaMemcpy(p.d_sb1_blk[i].p, p.sb1_blk_B[i].data(), p.sb1_blk_B[i].size() * 4,
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = p.d_sb2_blk[i].ensure(p.sb2_blk_B[i].size() * 4)) != cudaSuccess ||
+        (e = cudaMemcpy(p.d_sb2_blk[i].p, p.sb2_blk_B[i].data(), p.sb2_blk_B[i].size() * 4,
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_status(e);
+  }
   p.sb_dev_dirty = false;
   return DD_OK;
 }
@@ -365,7 +415,8 @@ dd_status dd_plan_set_tuning(dd_plan plan, int dms_per_block, int cc, int words)
   if (dms_per_block) t.dms_per_block = dms_per_block;
   if (cc) t.chans_per_chunk = cc;
   if (words) t.words_per_lane = words;
-  if (t.chans_per_chunk < 4 || t.chans_per_chunk > 32 || t.chans_per_chunk % 4)
+  if (t.chans_per_chunk < 4 || t.chans_per_chunk > 32 ||
+      (t.chans_per_chunk & (t.chans_per_chunk - 1)))
     return DD_ERR_INVALID_ARG;
   bool found = false;
   for (int i = 0; i < kNumTileCfgs; ++i)

@@ -109,7 +109,7 @@ def test_tuning_api():
     with pytest.raises(dd.DedispError):
         p.set_tuning(48, 8, 4)
     with pytest.raises(dd.DedispError):
-        p.set_tuning(32, 6, 4)
+        p.set_tuning(32, 12, 4)
 
 
 def test_execute_rejects_bad_arguments_without_a_gpu():
