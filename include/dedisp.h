@@ -180,6 +180,35 @@ dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void *in, int in_nb
                      int64_t in_row_stride_bytes, void *out,
                      int64_t out_row_stride_elems, void *cuda_stream, unsigned flags);
 
+/* ---- fixed-scratch execution */
+
+/* Bytes of the fixed device scratch array used by dd_execute_noalloc. */
+#define DD_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* The direct transform of dd_execute (device pointers, asynchronous on
+ * cuda_stream) for callers that must not allocate GPU memory: for example a
+ * real-time pipeline that reserves all of its device memory when it starts
+ * and cannot let a call allocate (or free, which synchronises the device)
+ * in the middle of an observation, or a host framework that owns all of the
+ * GPU's memory.  The paper has no counterpart to this call.
+ * Everything the kernels need besides the caller's input and output (staged
+ * image, delay and block tables, kill mask, status word) lives in one
+ * file-scope device array of DD_NOALLOC_SCRATCH_BYTES, which every GPU that
+ * loads the library holds until the process exits; the call itself allocates
+ * and frees nothing.  The first call on a device looks up the array's device
+ * address (set-up); make that first call before any stream capture.
+ * Returns DD_ERR_OOM, before launching anything, when the staged image and
+ * tables need more than the array (the image takes about nchans *
+ * (nsamps_out + max_delay) bytes per staged sample: half a byte for 1- and
+ * 2-bit input, 1, 2 or 4 bytes for 4-bit, 8-bit or float input).
+ * All calls share the array and each starts by reloading it: calls whose work
+ * overlaps on the GPU (other streams or threads) race, so the caller must
+ * serialise them.  Bound flags of this call are not reported by
+ * dd_plan_get_device_status. */
+dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const void *in_dev,
+                             int in_nbits, int64_t in_row_stride_bytes, void *out_dev,
+                             int64_t out_row_stride_elems, void *cuda_stream);
+
 /* ---- streaming: consecutive gulps of one beam (the overlap of Eq. 2) */
 
 /* A stream keeps the last max_delay input rows of its beam resident on the

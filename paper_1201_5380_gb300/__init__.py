@@ -63,6 +63,7 @@ def _load_lib():
         "dd_plan_get_kernel_timing": (I, [P, I, pp(D), pp(I64)]),
         "dd_plan_reset_kernel_timing": (I, [P]),
         "dd_execute": (I, [P, I64, P, I, I64, P, I64, P, ctypes.c_uint]),
+        "dd_execute_noalloc": (I, [P, I64, P, I, I64, P, I64, P]),
         "dd_stream_create": (I, [pp(P), P, I, I64]),
         "dd_stream_destroy": (None, [P]),
         "dd_stream_push": (I, [P, P, I64, I64, P, I64, pp(I64), P, ctypes.c_uint]),
@@ -278,6 +279,19 @@ class Plan:
         _check(_lib.dd_execute(self._h, int(nsamps_out), ip, int(nbits), int(istride), op,
                                int(ostride // 4), _stream_ptr(stream), flags), "dd_execute")
         return out
+
+
+def execute_noalloc(plan, inp, nbits, nsamps_out, out, stream=None):
+    """dd_execute_noalloc: the direct transform on device buffers without any
+    device allocation (fixed scratch array; see include/dedisp.h)."""
+    ip, istride, idev = _buf(inp)
+    op, ostride, odev = _buf(out)
+    if not (idev and odev):
+        raise ValueError("dd_execute_noalloc takes device buffers")
+    _check(_lib.dd_execute_noalloc(plan.handle, int(nsamps_out), ip, int(nbits), int(istride),
+                                   op, int(ostride // 4), _stream_ptr(stream)),
+           "dd_execute_noalloc")
+    return out
 
 
 class Stream:

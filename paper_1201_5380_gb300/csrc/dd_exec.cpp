@@ -225,7 +225,7 @@ dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
     const int bi = b_index(B);
     int32_t lo = j.plan->lo_B[bi];
     s.spread = j.plan->spread_B[bi];
-    s.seg.blk = static_cast<const int32_t*>(j.plan->d_blk[bi].p);
+    s.seg.blk = j.blk_dev ? j.blk_dev : static_cast<const int32_t*>(j.plan->d_blk[bi].p);
     s.seg.n_dmblk = (int32_t)j.plan->blocks_B[bi].size() - 1;
     if (!s.seg.blk) return DD_ERR_INVALID_ARG;
     s.seg.img = j.img;

@@ -221,6 +221,7 @@ struct DirectJob {
   void* out;
   int64_t out_stride;
   const Plan* plan;  // owner of the delay table (cached staging spreads)
+  const int32_t* blk_dev = nullptr;  // device block table; null = the plan's own
 };
 
 struct LaunchPlan {

@@ -1,0 +1,80 @@
+"""dd_execute_noalloc: the direct transform for callers that cannot allocate
+GPU memory (a real-time pipeline that reserves its device memory at start-up,
+a host framework that owns the GPU's memory).  It keeps its scratch in a
+fixed device array, so it must give the same results as dd_execute, and a
+second call in a row must not see the first call's leftovers.  This file is
+collected last so that a stop-at-first-failure run has already run the rest.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_1201_5380_gb300 as dd
+import synth
+from synth import configs
+from _gpu import torch_cuda
+
+pytestmark = pytest.mark.gpu
+F32_TOL = 1e-5
+
+
+def _call_noalloc(plan, d_in, nbits, nsamps, out, torch):
+    """Straight through the C ABI."""
+    return dd.lib().dd_execute_noalloc(
+        plan.handle, nsamps, d_in.data_ptr(), nbits, d_in.stride(0) * d_in.element_size(),
+        out.data_ptr(), out.stride(0), torch.cuda.current_stream().cuda_stream)
+
+
+def _both(plan, x, nbits, nsamps, torch):
+    d_in = torch.from_numpy(x).cuda()
+    dtype = torch.float32 if nbits == 32 else torch.int32
+    ref = torch.full((plan.dm_count, nsamps), -1, dtype=dtype, device="cuda")
+    got = torch.full((plan.dm_count, nsamps), -2, dtype=dtype, device="cuda")
+    plan.execute(d_in, nbits, nsamps, ref)
+    assert _call_noalloc(plan, d_in, nbits, nsamps, got, torch) == 0
+    torch.cuda.synchronize()
+    return got.cpu().numpy(), ref.cpu().numpy()
+
+
+def test_noalloc_matches_execute_on_consecutive_calls():
+    torch = torch_cuda()
+    c = configs.SURVEY
+    full = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
+    plan = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dms=full.dms[::12])
+    nsamps = 3000
+    rows = nsamps + plan.max_delay
+    for seed in (51, 52):  # two calls in a row, different data
+        x = synth.uniform_packed(seed, 0, rows, 1024, 2)
+        got, ref = _both(plan, x, 2, nsamps, torch)
+        assert np.array_equal(got, ref)
+
+
+def test_noalloc_small_u8_and_float_inputs():
+    torch = torch_cuda()
+    t = configs.TINY
+    plan = dd.Plan(t["nchans"], t["dt"], t["f0"], t["df"], dms=configs.linear_dms(t["dms"]))
+    rows = t["nsamps"] + plan.max_delay
+    for seed in (61, 62):
+        x = synth.normal_u8(seed, 0, rows, t["nchans"])
+        got, ref = _both(plan, x, 8, t["nsamps"], torch)
+        assert np.array_equal(got, ref)
+    xf = synth.normal_f32(63, 0, rows, t["nchans"])
+    got, ref = _both(plan, xf, 32, t["nsamps"], torch)
+    import oracle
+    delays = oracle.delay_table(t["nchans"], t["f0"], t["df"], t["dt"], plan.dms)
+    _, abssum = oracle.direct_f32(xf, t["nsamps"], delays)
+    assert np.all(np.abs(got.astype(np.float64) - ref) <= F32_TOL * abssum)
+
+
+def test_noalloc_rejects_problems_beyond_the_scratch():
+    torch = torch_cuda()
+    c = configs.SURVEY
+    plan = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
+    nsamps = 1 << 19   # staged image alone ~280 MB > the 64 MiB scratch
+    d_in = torch.zeros((nsamps + plan.max_delay, 256), dtype=torch.uint8, device="cuda")
+    out = torch.full((plan.dm_count, nsamps), 7, dtype=torch.int32, device="cuda")
+    rc = _call_noalloc(plan, d_in, 2, nsamps, out, torch)
+    assert rc == 5          # DD_ERR_OOM: rejected before anything is launched
+    torch.cuda.synchronize()
+    assert int(out.min()) == 7 and int(out.max()) == 7
