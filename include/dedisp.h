@@ -192,7 +192,7 @@ dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void *in, int in_nb
  * in the middle of an observation, or a host framework that owns all of the
  * GPU's memory.  The paper has no counterpart to this call.
  * Everything the kernels need besides the caller's input and output (staged
- * image, delay and block tables, kill mask, status word) lives in one
+ * image, trial-block and staging tables, kill mask, status word) lives in one
  * file-scope device array of DD_NOALLOC_SCRATCH_BYTES, which every GPU that
  * loads the library holds until the process exits; the call itself allocates
  * and frees nothing.  The first call on a device looks up the array's device

@@ -269,16 +269,21 @@ __device__ __forceinline__ int64_t window_word(int64_t t0, int32_t s0, int lo_sl
 
 // Shared-memory layout (32-bit words), two buffers of each region:
 //   [0,4)            two mbarriers
-//   landing[2][cc][nww+4]          TMA destination: raw image window
+//   landing[2][cc][nww+4]          TMA destination: raw image windows
 //   copies [2][cc*SPW][nww]        SPW lane-shifted copies of each window
-//   addr   [2][B*cc]               byte address of each (trial, channel)
+//   addr   [2][B*cc]               byte offset of each (trial, channel)
 //                                  window inside copies (lane 0, word 0)
 //
+// The staging tables are built on the host per plan and geometry (they do
+// not depend on the time tile): per (trial block, channel) the window start
+// and the words its trials read, and per (trial block, chunk) the B x cc
+// window offsets, which arrive by TMA with the chunk's windows.
+//
 // Per chunk (cc channels) of an item, one __syncthreads:
-//   prefetch next chunk's delays -> registers
-//   wait for this chunk's TMA; build its shifted copies from the landing area
+//   prefetch the next chunk's window records -> registers
+//   wait for this chunk's TMA; build its shifted copies (as far as read)
 //   __syncthreads
-//   warp 0 issues the next chunk's TMA; all threads write its address table
+//   warp 0 issues the next chunk's TMA (windows + offsets)
 //   shift-and-sum this chunk
 template <int FMT, int OUTK, bool WIDE, int NWARP, int DPW, int K>
 __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(const LaunchParams p) {
@@ -303,12 +308,14 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
   const int landing_words = cc * nwl;
   const int copy_words = COPIES ? cc * SPW * nww : 0;
   uint32_t* const s_addr = copies + 2 * copy_words;
+  const int n_entries = B << cc_log;  // offsets per chunk
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
-  // address-table entries of this thread: e = tid + r*NT, e < B*cc (r < 2)
-  const int n_entries = B << cc_log;
+  // the builder threads of a channel: NT / cc of them
+  const int tpc_log = (31 - __clz(NT)) - cc_log;
+  const int bc = tid >> tpc_log;
 
   if (tid == 0) {
     mbar_init(bar0, 1);
@@ -342,10 +349,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
     const int64_t t0 = tile * T;
     const int64_t t_end = min(t0 + T, S.nsamps);
     const int nchan = S.nchan;
-    const int dstride = S.delay_stride;
-    const int lo_slack = S.lo_slack;
     const int64_t row_words = S.row_words;
-    const int32_t* __restrict__ delays = S.delays + (int64_t)grp * S.g_delay;
     const uint32_t* __restrict__ img = S.img + (int64_t)grp * S.g_img;
     uint32_t* const out_g = reinterpret_cast<uint32_t*>(S.out) + (int64_t)grp * S.g_out;
     if (nd <= 0 || t0 >= S.nsamps) {
@@ -353,71 +357,46 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       continue;
     }
     const int nchunks = (nchan + cc - 1) >> cc_log;
+    // this item's staging tables
+    const int2* __restrict__ crec = reinterpret_cast<const int2*>(
+        S.crec + (int64_t)grp * S.g_crec + (int64_t)blk * nchan * 2);
+    const uint32_t* __restrict__ atab =
+        S.atab + (int64_t)grp * S.g_atab + (int64_t)blk * nchunks * n_entries;
+    const int64_t t0w = t0 / SPW;  // image word of time t0 - kPad
 
-    // Delays of this thread's address-table entries for chunk c0:
-    // entry e -> (slot = e >> cc_log, channel c = e & (cc-1)); s0 = first trial.
-    int32_t pf_s[2], pf_s0[2];
-    auto prefetch = [&](int c0) {
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int e = tid + r * NT;
-        pf_s[r] = pf_s0[r] = 0;
-        if (e < n_entries) {
-          const int slot = e >> cc_log;
-          const int cabs = min(c0 + (e & (cc - 1)), nchan - 1);
-          const int d = d0 + min(slot, nd - 1);
-          pf_s0[r] = __ldg(&delays[(int64_t)d0 * dstride + cabs]);
-          pf_s[r] = __ldg(&delays[(int64_t)d * dstride + cabs]);
-        }
-      }
+    // window record of channel c0 + (warp 0: lane; builders: bc) of chunk k
+    auto rec_of = [&](int k, int c) -> int2 {
+      const int ca = (k << cc_log) + c;
+      return ca < nchan ? __ldg(&crec[ca]) : make_int2(0, 32 * K);
     };
-    // Address table and TMA of chunk c0 into buffer nb (uses the prefetch).
-    auto issue = [&](int c0, int nb) {
-      uint32_t* const sa = s_addr + nb * n_entries;
-      const uint32_t copies_b = smem_addr(copies + nb * copy_words);
-      const uint32_t land_b = smem_addr(landing + nb * landing_words);
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int e = tid + r * NT;
-        if (e < n_entries) {
-          const int c = e & (cc - 1);
-          // zero window (c >= nchan): the build step clears it
-          uint32_t a = COPIES ? copies_b + (uint32_t)(c * SPW * nww) * 4u
-                              : land_b + (uint32_t)(c * nwl) * 4u;
-          if (c0 + c < nchan) {
-            const int64_t base = window_word<SPW>(t0, pf_s0[r], lo_slack) * SPW;
-            const int64_t o = t0 + kPad + (int64_t)pf_s[r] - base;
-            const int kap = (int)(o & (SPW - 1));
-            int64_t om = o / SPW;
-            if (o < 0 || om + 32 * K > nww) {
-              atomicOr(p.status, DEV_BAD_WINDOW);
-              om = 0;
-            }
-            a = COPIES ? copies_b + ((uint32_t)((c * SPW + kap) * nww) + (uint32_t)om) * 4u
-                       : land_b + ((uint32_t)(c * nwl) + (uint32_t)om) * 4u;
-          }
-          sa[e] = a;
-        }
+    // TMA of chunk k (warp 0): the offsets, then each channel's window.  A
+    // window running past the end of its row (a launch over images of
+    // different lengths) is shortened: those words are beyond every valid
+    // output of this image.
+    auto issue = [&](int k, int nb, int2 r) {
+      const uint32_t bar = bar0 + 8u * nb;
+      const int c0 = k << cc_log;
+      const int cabs = min(c0 + lane, nchan - 1);
+      int64_t wi = t0w + r.x;
+      const bool has = lane < cc && c0 + lane < nchan;
+      if (has && (wi < 0 || wi + 4 > row_words)) {
+        atomicOr(p.status, DEV_BAD_READ);
+        wi = 0;
       }
-      if (warp == 0) {
-        // Window of channel c0+lane; a window running past the end of its
-        // row (a launch over images of different lengths) is shortened: the
-        // words past the row are beyond every valid output of this image.
-        const uint32_t bar = bar0 + 8u * nb;
-        const int cabs = min(c0 + lane, nchan - 1);
-        int64_t wi = window_word<SPW>(t0, pf_s0[0], lo_slack);
-        if (lane < cc && (wi < 0 || wi + 4 > row_words)) {
-          atomicOr(p.status, DEV_BAD_READ);
-          wi = 0;
-        }
-        const uint32_t words = (uint32_t)min((int64_t)nwl, row_words - wi);
-        const uint32_t total = __reduce_add_sync(0xffffffffu, lane < cc ? words * 4u : 0u);
-        if (lane == 0) mbar_arrive_expect_tx(bar, total);
-        if (lane < cc) {
-          fence_proxy_async_smem();
-          tma_load_1d(smem_addr(landing + nb * landing_words + lane * nwl),
-                      img + (int64_t)cabs * row_words + wi, words * 4u, bar);
-        }
+      const uint32_t words = has ? (uint32_t)min((int64_t)nwl, row_words - wi) : 0u;
+      const uint32_t tab_bytes = (uint32_t)n_entries * 4u;
+      const uint32_t total = __reduce_add_sync(0xffffffffu, words * 4u) + tab_bytes;
+      if (lane == 0) {
+        mbar_arrive_expect_tx(bar, total);
+        fence_proxy_async_smem();
+        tma_load_1d(smem_addr(s_addr + nb * n_entries), atab + (int64_t)k * n_entries, tab_bytes,
+                    bar);
+      }
+      __syncwarp();
+      if (words) {
+        fence_proxy_async_smem();
+        tma_load_1d(smem_addr(landing + nb * landing_words + lane * nwl),
+                    img + (int64_t)cabs * row_words + wi, words * 4u, bar);
       }
     };
 
@@ -429,15 +408,21 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
     int g0 = 0, g1 = 0, g2 = 0;
 
     // prologue: chunk 0
-    prefetch(0);
-    issue(0, kk & 1);
+    int2 rec_w = make_int2(0, 0);  // warp 0: window record of the next chunk to issue
+    if (warp == 0) issue(0, kk & 1, rec_of(0, lane));
+    int span = COPIES ? rec_of(0, bc).y : 0;  // builders: words of this chunk's window
 
     for (int k = 0; k < nchunks; ++k, ++kk) {
       const int buf = kk & 1;
       const int c0 = k << cc_log;
       const bool more = k + 1 < nchunks;
-      if (more) prefetch(c0 + cc);
-      // (a) wait for the chunk's windows, then build the SPW shifted copies
+      int span_next = 0;
+      if (more) {
+        if (warp == 0) rec_w = rec_of(k + 1, lane);
+        if (COPIES) span_next = rec_of(k + 1, bc).y;
+      }
+      // (a) wait for the chunk's windows and offsets, then build the SPW
+      //     shifted copies as far as the chunk's trials read
       if (!mbar_wait_bounded(bar0 + 8u * buf, (kk >> 1) & 1u)) {
         atomicOr(p.status, DEV_TIMEOUT);
         mbar_wait_bounded(bar0 + 8u * buf, (kk >> 1) & 1u);
@@ -451,9 +436,8 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       } else {
         const uint32_t* const land = landing + buf * landing_words;
         uint32_t* const cp = copies + buf * copy_words;
-        const int tpc_log = (31 - __clz(NT)) - cc_log;  // threads per channel = NT / cc
-        const int c = tid >> tpc_log;
-        const int nq = nww >> 2;
+        const int c = bc;
+        const int nq = (min(span, nww) + 3) >> 2;
         const bool live = c0 + c < nchan;
         for (int q = tid & ((1 << tpc_log) - 1); q < nq; q += (1 << tpc_log)) {
           uint4 w = make_uint4(0u, 0u, 0u, 0u);
@@ -479,12 +463,14 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
         }
       }
       __syncthreads();
-      // (b) next chunk's address table and TMA (its buffers were released by
-      //     the barrier above)
-      if (more) issue(c0 + cc, buf ^ 1);
+      // (b) next chunk's TMA (its buffers were released by the barrier above)
+      if (more && warp == 0) issue(k + 1, buf ^ 1, rec_w);
+      span = span_next;
       // (c) shift-and-sum over the chunk, four channels per group
       const uint32_t* const sa = s_addr + buf * n_entries;
-      const uint32_t lane_off = (uint32_t)lane * 4u;
+      const uint32_t lane_off =
+          (COPIES ? smem_addr(copies + buf * copy_words) : smem_addr(landing + buf * landing_words)) +
+          (uint32_t)lane * 4u;
       for (int cg = 0; cg < cc; cg += 4) {
 #pragma unroll
         for (int i = 0; i < DPW; ++i) {

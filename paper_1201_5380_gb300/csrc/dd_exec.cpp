@@ -137,7 +137,104 @@ static void flush_periods(int fmt, int vmax, int nchan_max, bool* wide, int* f0,
 struct SegSpec {
   Seg seg;
   int32_t spread;
+  int kind;        // staging-table kind (0 direct, 1/2 sub-band stage)
+  Plan* owner;     // plan that caches the staging tables
+  TabSrc src;
+  bool no_upload;  // tables stay on the host (the caller places them)
+  StageTab* tab;   // set by finish_launch
 };
+
+// Staging tables (Seg::atab, Seg::crec) of one delay table.  For trial
+// block b and channel c the window starts at image word t0/SPW + woff,
+// woff = floor((kPad + s0 - lo) / (4 SPW)) * 4 with s0 the block's first
+// delay; trial slot i (slots past the block's last trial repeat it) reads
+// lane-shifted copy kap = o mod SPW from word o / SPW, o = kPad + s_i -
+// woff*SPW.  Absent channels of a last partial chunk read the zero window.
+static dd_status build_stage_tab(const TabSrc& src, int spw, int B, int K, int cc, int nww,
+                                 StageTab* t) {
+  const int nchunks = (src.nchan + cc - 1) / cc;
+  const bool copies = spw > 1;
+  const int nwl = nww + 4;
+  const int64_t per_blk = (int64_t)nchunks * B * cc;
+  t->g_atab = (int64_t)src.nblk * per_blk;
+  t->g_crec = (int64_t)src.nblk * src.nchan * 2;
+  t->atab.assign((size_t)(t->g_atab * src.ngroups), 0u);
+  t->crec.assign((size_t)(t->g_crec * src.ngroups), 0);
+  for (int g = 0; g < src.ngroups; ++g) {
+    const int32_t* dl = src.delays + (int64_t)g * src.g_delay;
+    const int32_t* bt = src.blk + (int64_t)g * (src.nblk + 1);
+    for (int b = 0; b < src.nblk; ++b) {
+      const int d0 = bt[b], d1 = bt[b + 1];
+      if (d1 <= d0) continue;  // padding block: never visited
+      uint32_t* at = t->atab.data() + g * t->g_atab + b * per_blk;
+      int32_t* cr = t->crec.data() + g * t->g_crec + (int64_t)b * src.nchan * 2;
+      for (int c = 0; c < nchunks * cc; ++c) {
+        const int cl = c % cc;
+        uint32_t* a = at + (int64_t)(c / cc) * B * cc + cl;
+        if (c >= src.nchan) {
+          const uint32_t zero = (uint32_t)(copies ? cl * spw * nww : cl * nwl) * 4u;
+          for (int i = 0; i < B; ++i) a[(int64_t)i * cc] = zero;
+          continue;
+        }
+        const int64_t b0 = (int64_t)kPad + dl[(int64_t)d0 * src.dstride + c] - src.lo;
+        if (b0 < 0) return DD_ERR_INVALID_ARG;
+        const int64_t woff = b0 / (4 * spw) * 4;
+        int64_t span = 0;
+        for (int i = 0; i < B; ++i) {
+          const int d = std::min(d0 + i, d1 - 1);
+          const int64_t o = (int64_t)kPad + dl[(int64_t)d * src.dstride + c] - woff * spw;
+          const int64_t om = o / spw;
+          if (o < 0 || om + 32 * K > nww) return DD_ERR_INVALID_ARG;
+          const int64_t kap = o & (spw - 1);
+          span = std::max<int64_t>(span, om + 32 * K);
+          a[(int64_t)i * cc] =
+              (uint32_t)(copies ? ((cl * spw + kap) * nww + om) * 4 : (cl * nwl + om) * 4);
+        }
+        cr[2 * c] = (int32_t)woff;
+        cr[2 * c + 1] = (int32_t)span;
+      }
+    }
+  }
+  return DD_OK;
+}
+
+StageTab* stage_tab(Plan& p, int kind, const TabSrc& src, int spw, int B, int K, int cc,
+                    int nww, bool upload, dd_status* err) {
+  const std::array<int, 7> key = {kind, B, spw, K, cc, nww, src.lo};
+  auto it = p.tabs.find(key);
+  if (it == p.tabs.end()) {
+    if (p.tabs.size() >= 16) p.tabs.clear();  // bounded cache (frees synchronise the device)
+    std::unique_ptr<StageTab> t(new StageTab);
+    *err = build_stage_tab(src, spw, B, K, cc, nww, t.get());
+    if (*err != DD_OK) return nullptr;
+    it = p.tabs.emplace(key, std::move(t)).first;
+  }
+  StageTab* t = it->second.get();
+  if (upload && !t->uploaded) {
+    cudaError_t e = t->d_atab.ensure(t->atab.size() * 4);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(t->d_atab.p, t->atab.data(), t->atab.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = t->d_crec.ensure(t->crec.size() * 4);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(t->d_crec.p, t->crec.data(), t->crec.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      *err = cuda_status(e);
+      return nullptr;
+    }
+    t->uploaded = true;
+  }
+  *err = DD_OK;
+  return t;
+}
+
+void drop_stage_tabs(Plan& p, int kind_mask) {
+  for (auto it = p.tabs.begin(); it != p.tabs.end();) {
+    if (kind_mask & (1 << it->first[0]))
+      it = p.tabs.erase(it);
+    else
+      ++it;
+  }
+}
 
 // Fill launch parameters for a set of segments sharing one staged format.
 static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector<SegSpec>& specs,
@@ -196,6 +293,25 @@ static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector
   lp.f2 = f2;
   lp.n_items = items;
   lp.vec_out = vec_out ? 1 : 0;
+  // staging tables of each segment for this geometry
+  {
+    size_t i = 0;
+    for (auto& sp : specs) {
+      if (sp.seg.ndm <= 0 || sp.seg.nsamps <= 0) continue;
+      dd_status err;
+      StageTab* t = stage_tab(*sp.owner, sp.kind, sp.src, fmt_spw(fmt), B,
+                              kTileCfgs[cfg].k, cc, nww, !sp.no_upload, &err);
+      if (!t) return err;
+      sp.tab = t;
+      Seg& g = lp.segs[i];
+      g.atab = sp.no_upload ? nullptr : static_cast<const uint32_t*>(t->d_atab.p);
+      g.crec = sp.no_upload ? nullptr : static_cast<const int32_t*>(t->d_crec.p);
+      g.g_atab = t->g_atab;
+      g.g_crec = t->g_crec;
+      L->segs[i] = g;
+      ++i;
+    }
+  }
   L->smem = dedisp_smem_bytes(fmt, cfg, cc, nww);
   int per_sm = 0;
   cudaError_t e = dedisp_max_blocks_per_sm(fmt, outk, wide, cfg, L->smem, &per_sm);
@@ -214,7 +330,8 @@ dd_status run_launch(Plan& p, LaunchPlan& L, cudaStream_t st) {
 }
 
 dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
-                             const std::vector<DirectJob>& jobs, LaunchPlan* L) {
+                             const std::vector<DirectJob>& jobs, LaunchPlan* L,
+                             std::vector<StageTab*>* tabs) {
   const int cfg = tile_cfg_index(p.tune);
   const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
   std::vector<SegSpec> specs;
@@ -242,9 +359,20 @@ dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
     s.seg.ndm_last = j.ndm;
     if (lo > kPad) return DD_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(j.out) & 15) || (j.out_stride & 3)) vec = false;
+    s.kind = 0;
+    s.owner = const_cast<Plan*>(j.plan);
+    const std::vector<int32_t>& bl = j.plan->blocks_B[bi];
+    s.src = TabSrc{j.plan->delays.data(), 0, j.nchans, j.nchans, 1, bl.data(),
+                   (int)bl.size() - 1, lo};
+    s.no_upload = j.no_upload;
     specs.push_back(s);
   }
-  return finish_launch(p, fmt, outk, vmax, specs, vec, L);
+  dd_status st = finish_launch(p, fmt, outk, vmax, specs, vec, L);
+  if (st == DD_OK && tabs) {
+    tabs->clear();
+    for (auto& sp : specs) tabs->push_back(sp.tab);
+  }
+  return st;
 }
 
 // Geometry of the staged input image for a direct job: large enough for
@@ -402,6 +530,10 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
     g.nsamps = len1;
     g.out = S + (half ? kPad / 2 : kPad);
     g.out_stride = (int64_t)nsb * rw2;
+    sp.kind = 1;
+    sp.owner = &p;
+    sp.src = TabSrc{p.sb_rel.data(), Np, C, Np, nsb, p.sb1_blk_B[bi].data(), p.sb1_nblk_B[bi],
+                    lo1};
   }
   LaunchPlan L1;
   s = finish_launch(p, fmt, half ? OUT_HALFIMG : OUT_U32, vmax_in, specs, true, &L1);
@@ -432,6 +564,10 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
     q.nsamps = G;
     q.out = a.out;
     q.out_stride = a.out_stride;
+    sp.kind = 2;
+    sp.owner = &p;
+    sp.src = TabSrc{p.sb_d2.data(), (int64_t)p.sb_dms * nsb, nsb, nsb, ng,
+                    p.sb2_blk_B[bi].data(), p.sb2_nblk_B[bi], lo2};
   }
   const bool vec = !(reinterpret_cast<uintptr_t>(a.out) & 15) && !(a.out_stride & 3);
   LaunchPlan L2;

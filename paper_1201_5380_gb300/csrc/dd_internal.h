@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
+#include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -74,6 +77,13 @@ struct Seg {
   int32_t delay_stride;   // elements between trial rows of the delay table
   int32_t nchan;          // channels summed
   int32_t lo_slack;       // max_{block,c} delay(d0,c) - min_{d in block} delay(d,c)
+  // Staging tables of the launch geometry (built on the host, see StageTab):
+  const uint32_t* atab;   // [group][block][chunk][trial slot][channel of chunk]
+                          // byte offset of the (trial, channel) window
+  const int32_t* crec;    // [group][block][channel] {window start word - t0/SPW,
+                          // words of the window the block's trials read}
+  int64_t g_atab;         // per-group offsets of the two tables (elements)
+  int64_t g_crec;
 };
 
 constexpr int kMaxSegs = 32;  // segments per launch, passed inline as a kernel parameter
@@ -128,6 +138,29 @@ struct Tuning {
   int words_per_lane = 4;
 };
 
+// Staging tables of one delay table for one launch geometry.  They do not
+// depend on the time tile: a tile starts on a multiple of 4*SPW samples, so
+// each (trial block, channel) window starts at t0/SPW + woff image words and
+// every trial's offset inside it is fixed.
+struct StageTab {
+  bool uploaded = false;
+  std::vector<uint32_t> atab;  // see Seg::atab
+  std::vector<int32_t> crec;   // see Seg::crec (pairs)
+  int64_t g_atab = 0, g_crec = 0;
+  DevBuf d_atab, d_crec;
+};
+
+// Where a stage table's delays come from (host copies).
+struct TabSrc {
+  const int32_t* delays;  // group 0, trial 0, channel 0
+  int64_t g_delay;        // per-group offset (elements)
+  int dstride;            // elements between trial rows
+  int nchan, ngroups;
+  const int32_t* blk;     // per-group block starts, nblk+1 entries per group
+  int nblk;
+  int lo;                 // lo_slack of the blocks
+};
+
 struct Plan {
   int device = 0;
   int nchans = 0;
@@ -162,6 +195,10 @@ struct Plan {
   std::vector<int32_t> sb1_blk_B[3], sb2_blk_B[3];
   int32_t sb1_nblk_B[3] = {0, 0, 0}, sb2_nblk_B[3] = {0, 0, 0};
   DevBuf d_sb1_blk[3], d_sb2_blk[3];
+  // staging tables: key {kind (0 direct, 1/2 sub-band stage), B, SPW, K,
+  // cc, nww, lo_slack}.  An entry is never rebuilt in place (a launch on
+  // another stream may still read it); entries go when the delays change.
+  std::map<std::array<int, 7>, std::unique_ptr<StageTab>> tabs;
   // kernel timing (dd_plan_set_kernel_timing)
   bool timing = false;
   struct TimedLaunch {
@@ -222,6 +259,7 @@ struct DirectJob {
   int64_t out_stride;
   const Plan* plan;  // owner of the delay table (cached staging spreads)
   const int32_t* blk_dev = nullptr;  // device block table; null = the plan's own
+  bool no_upload = false;  // leave staging tables on the host (caller places them)
 };
 
 struct LaunchPlan {
@@ -250,8 +288,15 @@ void make_blocks(const int32_t* delays, int ndm, int nchans, int stride, int B,
 constexpr int32_t kSpreadBudget = 4400;
 int time_tile(int fmt, const Tuning& t);
 dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
-                             const std::vector<DirectJob>& jobs, LaunchPlan* lpl);
+                             const std::vector<DirectJob>& jobs, LaunchPlan* lpl,
+                             std::vector<StageTab*>* tabs = nullptr);
 dd_status run_launch(Plan& p, LaunchPlan& lpl, cudaStream_t st);
+// The plan's staging tables of `src` (kind 0 direct, 1/2 sub-band stage)
+// for a launch geometry, built on first use and uploaded when asked; null
+// with *err set if a window would not fit the geometry.
+StageTab* stage_tab(Plan& p, int kind, const TabSrc& src, int spw, int B, int K, int cc,
+                    int nww, bool upload, dd_status* err);
+void drop_stage_tabs(Plan& p, int kind_mask);
 dd_status stage_direct_image(Plan& p, const void* in, int nbits, int64_t in_stride, int64_t rows,
                              int64_t nsamps, DevBuf& image, cudaStream_t st, DirectJob* j);
 

@@ -1,7 +1,8 @@
 // dd_execute_noalloc: the direct transform for callers that may not allocate
 // device memory.  Everything the kernels need besides the caller's input and
-// output (staged image, delay and block tables, kill mask, status word) lives
-// in one fixed file-scope device array, so no call allocates or frees.
+// output (staged image, trial-block and staging tables, kill mask, status
+// word) lives in one fixed file-scope device array, so no call allocates or
+// frees.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -61,28 +62,53 @@ extern "C" dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const 
   if (in_row_stride < row_bytes) return DD_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(p->mu);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  unsigned char* sc = nullptr;
+  dd_status s = scratch_for_current_device(&sc);
+  if (s != DD_OK) return s;
 
-  // Layout of the scratch for this call; reject problems that do not fit.
+  // Plan the launch first, with the staging tables left on the host: they
+  // size the scratch.  Device pointers are patched in once it is laid out.
   const int cfg = tile_cfg_index(p->tune);
   const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
   const int bi = b_index(B);
   const std::vector<int32_t>& blocks = p->blocks_B[bi];
   const int64_t rw = image_row_words(fmt, p->tune, nsamps_out, p->max_delay, p->spread_B[bi]);
+  DirectJob j;
+  j.img = reinterpret_cast<const uint32_t*>(sc);
+  j.row_words = rw;
+  j.img_row_samples = rw * fmt_spw(fmt);
+  j.d_delays = nullptr;
+  j.h_delays = p->delays.data();
+  j.nchans = p->nchans;
+  j.ndm = ndm(*p);
+  j.nsamps = nsamps_out;
+  j.out = out;
+  j.out_stride = out_stride;
+  j.plan = p;
+  j.blk_dev = reinterpret_cast<const int32_t*>(sc);
+  j.no_upload = true;
+  LaunchPlan L;
+  std::vector<StageTab*> tabs;
+  s = plan_direct_launch(*p, fmt, fmt == FMT_F32 ? OUT_F32 : OUT_U32, vmax_for_nbits(in_nbits),
+                         {j}, &L, &tabs);
+  if (s != DD_OK) return s;
+  if (L.lp.n_items == 0) return DD_OK;
+  const StageTab* t = tabs.at(0);
+
+  // Layout of the scratch for this call; reject problems that do not fit.
   const size_t off_status = 0;
   const size_t off_mask = 256;
-  const size_t off_delays = off_mask + round256((size_t)p->nchans);
-  const size_t off_blocks = off_delays + round256(p->delays.size() * sizeof(int32_t));
-  const size_t off_image = off_blocks + round256(blocks.size() * sizeof(int32_t));
+  const size_t off_blocks = off_mask + round256((size_t)p->nchans);
+  const size_t off_atab = off_blocks + round256(blocks.size() * sizeof(int32_t));
+  const size_t off_crec = off_atab + round256(t->atab.size() * sizeof(uint32_t));
+  const size_t off_image = off_crec + round256(t->crec.size() * sizeof(int32_t));
   const size_t need = off_image + (size_t)p->nchans * (size_t)rw * 4u;
   if (need > (size_t)DD_NOALLOC_SCRATCH_BYTES) return DD_ERR_OOM;
-
-  unsigned char* sc = nullptr;
-  dd_status s = scratch_for_current_device(&sc);
-  if (s != DD_OK) return s;
   uint32_t* status = reinterpret_cast<uint32_t*>(sc + off_status);
   uint8_t* mask = sc + off_mask;
-  int32_t* delays = reinterpret_cast<int32_t*>(sc + off_delays);
   int32_t* blk = reinterpret_cast<int32_t*>(sc + off_blocks);
+  uint32_t* atab = reinterpret_cast<uint32_t*>(sc + off_atab);
+  int32_t* crec = reinterpret_cast<int32_t*>(sc + off_crec);
   uint32_t* img = reinterpret_cast<uint32_t*>(sc + off_image);
 
   // The array keeps the previous call's contents: reset the status word and
@@ -91,10 +117,13 @@ extern "C" dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const 
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(mask, p->mask.data(), (size_t)p->nchans, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(delays, p->delays.data(), p->delays.size() * sizeof(int32_t),
+    e = cudaMemcpyAsync(blk, blocks.data(), blocks.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(blk, blocks.data(), blocks.size() * sizeof(int32_t),
+    e = cudaMemcpyAsync(atab, t->atab.data(), t->atab.size() * sizeof(uint32_t),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(crec, t->crec.data(), t->crec.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_status(e);
 
@@ -103,24 +132,11 @@ extern "C" dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const 
                          p->nchans, mask, img, rw, rw, st);
   if (e != cudaSuccess) return cuda_status(e);
 
-  DirectJob j;
-  j.img = img;
-  j.row_words = rw;
-  j.img_row_samples = rw * fmt_spw(fmt);
-  j.d_delays = delays;
-  j.h_delays = p->delays.data();
-  j.nchans = p->nchans;
-  j.ndm = ndm(*p);
-  j.nsamps = nsamps_out;
-  j.out = out;
-  j.out_stride = out_stride;
-  j.plan = p;
-  j.blk_dev = blk;
-  LaunchPlan L;
-  s = plan_direct_launch(*p, fmt, fmt == FMT_F32 ? OUT_F32 : OUT_U32, vmax_for_nbits(in_nbits),
-                         {j}, &L);
-  if (s != DD_OK) return s;
-  if (L.lp.n_items == 0) return DD_OK;
+  Seg& g = L.lp.segs[0];
+  g.img = img;
+  g.blk = blk;
+  g.atab = atab;
+  g.crec = crec;
   L.lp.status = status;
   return cuda_status(launch_dedisp(L.fmt, L.outk, L.wide, L.cfg, L.lp, L.grid, L.smem, st));
 }

@@ -108,6 +108,7 @@ static dd_status build_delays(Plan& p) {
   p.blk_dirty = true;
   p.delays_dirty = true;
   p.sb_dirty = true;
+  drop_stage_tabs(p, 7);
   return DD_OK;
 }
 
@@ -243,6 +244,7 @@ dd_status prepare_subband(Plan& p) {
   }
   p.sb_dirty = false;
   p.sb_dev_dirty = true;
+  drop_stage_tabs(p, 6);
   return DD_OK;
 }
 
