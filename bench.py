@@ -44,7 +44,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gulp", type=int, default=0,
                     help="samples per gulp (default: the workload's 2^19); smaller values "
@@ -122,6 +122,11 @@ class ClockSampler:
 
 # ------------------------------------------------------------ cpu oracle
 
+# DRAM bytes (read + write) of one dedispersion launch on the survey band at
+# 2^17 output samples, from ncu; the traffic grows in proportion to the gulp.
+DEDISP_TRAFFIC_2E17 = 80.128256e6 + 569.433344e6
+
+
 def cpu_oracle_rate(x, delays, G, seconds):
     """Time the CPU oracle (as it stands) on a bounded sample of the workload:
     trials evenly spaced over the list, all channels, a prefix of the gulp.
@@ -134,13 +139,19 @@ def cpu_oracle_rate(x, delays, G, seconds):
     oracle.direct(x, 2, nchans, 2048, delays[probe_d])
     dt = max(time.perf_counter() - t0, 1e-3)
     rate = 8 * 2048 * nchans / dt
-    want = rate * seconds
-    ntr = int(min(delays.shape[0], max(8, want // (nchans * 16384))))
-    ns = int(min(G, max(2048, want // (nchans * ntr))))
-    sel = np.linspace(0, delays.shape[0] - 1, ntr).astype(int)
-    t0 = time.perf_counter()
-    oracle.direct(x, 2, nchans, ns, delays[sel])
-    dt = time.perf_counter() - t0
+    # the small probe underestimates the threaded rate: size a first sample
+    # to a fraction of the budget, then rescale once from its own rate
+    budget = seconds / 4.0
+    for _ in range(2):
+        want = rate * budget
+        ntr = int(min(delays.shape[0], max(8, want // (nchans * 16384))))
+        ns = int(min(G, max(2048, want // (nchans * ntr))))
+        sel = np.linspace(0, delays.shape[0] - 1, ntr).astype(int)
+        t0 = time.perf_counter()
+        oracle.direct(x, 2, nchans, ns, delays[sel])
+        dt = time.perf_counter() - t0
+        rate = float(ntr) * ns * nchans / max(dt, 1e-3)
+        budget = seconds
     adds = float(ntr) * ns * nchans
     desc = "%d of %d trials (evenly spaced) x %d of %d samples x %d channels" % (
         ntr, delays.shape[0], ns, G, nchans)
@@ -298,7 +309,11 @@ def run_ours(a, rank, world, local_rank):
         "gpu_launches": int(dd_n + ct_n),
         "kernels_ms_per_step": {"dedisp": k_ms, "corner_turn": ct_ms / max(ct_n, 1)},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12,
-                     "unit": "Tadd/s", "frac": achieved / peak_adds, "traffic": None,
+                     "unit": "Tadd/s", "frac": achieved / peak_adds,
+                     "traffic": DEDISP_TRAFFIC_2E17 * G / 131072.0,
+                     "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                       "ncu capture at 2^17 samples, scaled by the gulp "
+                                       "(profiles/k_dedisp_survey_ncu_full.md)",
                      "peak_source": "measured integer-add probe (dd_probe_int_add)",
                      "byte_floor_ms": byte_floor_ms, "compute_floor_ms": units / peak_adds * 1e3,
                      "hbm_gbs_used": hbm},
