@@ -258,6 +258,85 @@ dd_status dd_batch_add(dd_batch batch, dd_stream stream, const void *in_dev,
  * (asynchronous); nsamps_out[i] receives the outputs of the i-th add. */
 dd_status dd_batch_launch(dd_batch batch, void *cuda_stream, int64_t *nsamps_out);
 
+/* ---- serving: gulps of many beams as they arrive (continuous batching)
+ *
+ * The paper processes fixed blocks one at a time and has no serving layer;
+ * this engine applies the streaming transform above to many beams at once.
+ * A server owns one device arena, allocated when it is created, from which
+ * each admitted gulp takes an input buffer and an output buffer.  Gulps are
+ * queued by dd_server_submit and admitted by dd_server_step as in-flight
+ * launches retire and arena space frees up: at most one gulp per beam per
+ * launch, a beam's gulps strictly in submission order, at most max_batch
+ * gulps per launch and max_inflight launches queued on the GPU.  Each launch
+ * copies its inputs in on a copy stream, runs every admitted beam's
+ * transform as one batched persistent launch (dd_batch_launch) on the
+ * compute stream, and copies outputs out on a second copy stream, so the
+ * copies of one launch overlap the compute of another.  Results are those
+ * of dd_stream_push on the same beam, bit for bit. */
+typedef struct dd_server_s *dd_server;
+
+/* Completed request, as returned by dd_server_poll. */
+typedef struct {
+  uint64_t request;     /* id returned by dd_server_submit */
+  int beam;             /* beam id returned by dd_server_add_beam */
+  int status;           /* dd_status of the request */
+  int64_t nsamps_out;   /* output samples per trial (0 while the beam's
+                           overlap tail is still filling) */
+  const void *out_dev;  /* device output rows (uint32, or float for 32-bit
+                           input), row stride out_stride; valid until
+                           dd_server_release; null when copied to host_out */
+  int64_t out_stride;   /* elements */
+  double latency_ms;    /* dd_server_submit -> output ready on the GPU (or
+                           in host_out when one was given) */
+} dd_request_info;
+
+/* Create a server on the current device with an arena of arena_bytes
+ * (allocated here, once), at most max_batch (1..32) gulps per launch and
+ * max_inflight (1..8) launches queued on the GPU. */
+dd_status dd_server_create(dd_server *server, size_t arena_bytes, int max_batch,
+                           int max_inflight);
+/* Waits for every launch in flight, then frees the server, its streams and
+ * its arena (plans stay with the caller). */
+void dd_server_destroy(dd_server server);
+
+/* Register a beam: its plan (band, DM list; must outlive the server), input
+ * bits and largest gulp.  The beam keeps its overlap tail on the device. */
+dd_status dd_server_add_beam(dd_server server, dd_plan plan, int in_nbits, int64_t max_gulp,
+                             int *beam);
+
+/* Queue one gulp of nsamps_in rows (host memory, row stride
+ * in_row_stride_bytes; page-locked memory lets the copy run asynchronously).
+ * in_host must stay valid, unchanged, until the request completes.  host_out
+ * (optional, null for device output) receives the output rows with row
+ * stride out_row_stride_elems >= nsamps_in.  Non-blocking.  Returns
+ * DD_ERR_REJECTED when the gulp's buffers could never fit in the arena. */
+dd_status dd_server_submit(dd_server server, int beam, const void *in_host, int64_t nsamps_in,
+                           int64_t in_row_stride_bytes, void *host_out,
+                           int64_t out_row_stride_elems, uint64_t *request);
+
+/* One scheduling pass: retire launches that finished, admit queued gulps
+ * and launch them.  With wait != 0 and nothing admissible it first waits
+ * for the oldest launch in flight.  *admitted (may be null) receives the
+ * gulps launched by this pass. */
+dd_status dd_server_step(dd_server server, int wait, int *admitted);
+
+/* Up to max completed requests, oldest first; *n receives the count. */
+dd_status dd_server_poll(dd_server server, dd_request_info *out, int max, int *n);
+
+/* Copy a completed request's device output into host rows of stride
+ * host_row_stride_elems (synchronous). */
+dd_status dd_server_copy_out(dd_server server, uint64_t request, void *host_dst,
+                             int64_t host_row_stride_elems);
+
+/* Return a completed request's device output to the arena.  Requests that
+ * had a host_out are forgotten once polled and need no release. */
+dd_status dd_server_release(dd_server server, uint64_t request);
+
+/* Queued, in-flight and completed-but-unreleased requests, and arena bytes
+ * in use (any pointer may be null). */
+dd_status dd_server_stats(dd_server server, int *queued, int *inflight, int *completed,
+                          size_t *arena_used);
+
 /* ---- measurement */
 
 /* Integer-add throughput of the current device, measured by a kernel of

@@ -77,6 +77,15 @@ def _load_lib():
         "dd_batch_add": (I, [P, P, P, I64, I64, P, I64]),
         "dd_batch_launch": (I, [P, P, P]),
         "dd_probe_int_add": (I, [I64, P, pp(D), pp(D)]),
+        "dd_server_create": (I, [pp(P), ctypes.c_size_t, I, I]),
+        "dd_server_destroy": (None, [P]),
+        "dd_server_add_beam": (I, [P, P, I, I64, pp(I)]),
+        "dd_server_submit": (I, [P, I, P, I64, I64, P, I64, pp(ctypes.c_uint64)]),
+        "dd_server_step": (I, [P, I, pp(I)]),
+        "dd_server_poll": (I, [P, P, I, pp(I)]),
+        "dd_server_copy_out": (I, [P, ctypes.c_uint64, P, I64]),
+        "dd_server_release": (I, [P, ctypes.c_uint64]),
+        "dd_server_stats": (I, [P, pp(I), pp(I), pp(I), pp(ctypes.c_size_t)]),
     }
     for name, (res, args) in sigs.items():
         try:
@@ -387,6 +396,99 @@ class Batch:
         _check(_lib.dd_batch_launch(self._h, _stream_ptr(stream), n.ctypes.data),
                "dd_batch_launch")
         return n[:self._n]
+
+
+class RequestInfo(ctypes.Structure):
+    """A completed serving request (dd_request_info)."""
+    _fields_ = [("request", ctypes.c_uint64), ("beam", ctypes.c_int), ("status", ctypes.c_int),
+                ("nsamps_out", ctypes.c_int64), ("out_dev", ctypes.c_void_p),
+                ("out_stride", ctypes.c_int64), ("latency_ms", ctypes.c_double)]
+
+
+class Server:
+    """Serving engine: gulps of many beams, admitted into batched launches
+    as launches retire and arena memory frees up (dd_server_*)."""
+
+    def __init__(self, arena_bytes, max_batch=16, max_inflight=2):
+        h = ctypes.c_void_p()
+        _check(_lib.dd_server_create(ctypes.byref(h), int(arena_bytes), int(max_batch),
+                                     int(max_inflight)), "dd_server_create")
+        self._h = h
+        self._keep = {}  # request -> host buffers that must outlive it
+        self._ndm = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dd_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_beam(self, plan, nbits, max_gulp):
+        b = ctypes.c_int()
+        _check(_lib.dd_server_add_beam(self._h, plan.handle, int(nbits), int(max_gulp),
+                                       ctypes.byref(b)), "dd_server_add_beam")
+        self._ndm[b.value] = plan.dm_count
+        return b.value
+
+    def submit(self, beam, inp, nsamps_in=None, out=None):
+        """Queue one gulp from a host array ``inp`` (rows); ``out`` (host,
+        optional) receives the output rows.  Returns the request id."""
+        ip, istride, idev = _buf(inp)
+        if idev:
+            raise ValueError("the server takes gulps from host memory")
+        n = int(inp.shape[0] if nsamps_in is None else nsamps_in)
+        op, ostride = None, 0
+        if out is not None:
+            op, ob, odev = _buf(out)
+            if odev:
+                raise ValueError("host_out must be host memory")
+            ostride = ob // 4
+        r = ctypes.c_uint64()
+        _check(_lib.dd_server_submit(self._h, int(beam), ip, n, int(istride), op, int(ostride),
+                                     ctypes.byref(r)), "dd_server_submit")
+        self._keep[r.value] = (inp, out)
+        return r.value
+
+    def step(self, wait=False):
+        n = ctypes.c_int()
+        _check(_lib.dd_server_step(self._h, 1 if wait else 0, ctypes.byref(n)), "dd_server_step")
+        return n.value
+
+    def poll(self, max_n=256):
+        arr = (RequestInfo * max_n)()
+        n = ctypes.c_int()
+        _check(_lib.dd_server_poll(self._h, arr, int(max_n), ctypes.byref(n)), "dd_server_poll")
+        res = []
+        for i in range(n.value):
+            a = arr[i]
+            self._keep.pop(a.request, None)
+            res.append(dict(request=a.request, beam=a.beam, status=a.status,
+                            nsamps_out=a.nsamps_out, out_dev=a.out_dev,
+                            out_stride=a.out_stride, latency_ms=a.latency_ms))
+        return res
+
+    def copy_out(self, request, host):
+        p, stride, dev = _buf(host)
+        if dev:
+            raise ValueError("copy_out writes host memory")
+        _check(_lib.dd_server_copy_out(self._h, int(request), p, int(stride // 4)),
+               "dd_server_copy_out")
+
+    def release(self, request):
+        _check(_lib.dd_server_release(self._h, int(request)), "dd_server_release")
+
+    def stats(self):
+        q, f, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        u = ctypes.c_size_t()
+        _check(_lib.dd_server_stats(self._h, ctypes.byref(q), ctypes.byref(f), ctypes.byref(c),
+                                    ctypes.byref(u)), "dd_server_stats")
+        return dict(queued=q.value, inflight=f.value, completed=c.value, arena_used=u.value)
 
 
 def probe_int_add(adds_per_thread=1 << 16, stream=None):

@@ -122,3 +122,15 @@ def test_execute_rejects_bad_arguments_without_a_gpu():
     with pytest.raises(dd.DedispError) as e:
         p.execute(a, 8, 20, o)                     # output row shorter than nsamps
     assert e.value.code == 1
+
+
+def test_server_api_validates_without_a_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("checks the no-device error path")
+    with pytest.raises(dd.DedispError):
+        dd.Server(arena_bytes=0)                   # arena too small
+    with pytest.raises(dd.DedispError):
+        dd.Server(arena_bytes=1 << 20, max_batch=33)
+    with pytest.raises(dd.DedispError):
+        dd.Server(arena_bytes=1 << 20)             # no device to bind
