@@ -46,6 +46,7 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--gulp", type=int, default=0,
                     help="samples per gulp (default: the workload's 2^19); smaller values "
                          "are for profiler captures, not bench lines")
@@ -203,6 +204,163 @@ def run_reference(a, rank, world):
 
 # -------------------------------------------------------------------- ours
 
+def _serve_all(srv, plans, beams, reqs, host, t_sched=None):
+    """Submit requests (beam index, gulp) at their scheduled times (all at
+    once without a schedule), drive the server until every one completed and
+    return per-request (arrival -> ready ms, output units)."""
+    order = list(range(len(reqs)))
+    if t_sched is not None:
+        order.sort(key=lambda i: t_sched[i])
+    lag, ids = {}, {}
+    res = []
+    t0 = time.perf_counter()
+    i = 0
+    while len(res) < len(reqs):
+        now = time.perf_counter() - t0
+        progressed = False
+        while i < len(order) and (t_sched is None or t_sched[order[i]] <= now):
+            k = order[i]
+            b, g = reqs[k]
+            nch = plans[b].nchans
+            r = srv.submit(beams[b], host[nch][:g], g)
+            ids[r] = k
+            lag[k] = 0.0 if t_sched is None else (time.perf_counter() - t0 - t_sched[k]) * 1e3
+            i += 1
+            progressed = True
+        progressed |= srv.step() > 0
+        for info in srv.poll():
+            if info["status"] != 0:
+                raise RuntimeError("serving request failed: status %d" % info["status"])
+            k = ids[info["request"]]
+            b = reqs[k][0]
+            res.append((lag[k] + info["latency_ms"],
+                        float(plans[b].nchans) * plans[b].dm_count * info["nsamps_out"]))
+            if info["out_dev"]:
+                srv.release(info["request"])
+            progressed = True
+        if not progressed:
+            if i >= len(order):
+                srv.step(wait=True)
+            else:
+                time.sleep(0.0002)
+    return res
+
+
+def run_serving(a):
+    """The serving workload: 13 beams (512- and 1024-channel bands by turn,
+    8-bit samples, trial DMs 0-2000 by the bounded-smearing rule), gulps
+    uniform in 2^16..2^19 samples, Poisson arrivals per beam at 70 % of the
+    measured batched capacity; outputs stay on the device (a downstream
+    search stage consumes them) and are released on completion."""
+    import torch
+    import paper_1201_5380_gb300 as dd
+
+    c = configs.SERVING
+    rng = np.random.default_rng(c["seed"])
+    plans = []
+    for b in range(c["nbeams"]):
+        band = c["bands"][b % 2]
+        plans.append(dd.Plan(band["nchans"], c["dt"], band["f0"], band["df"],
+                             dm_rule=dict(lo=c["dms"]["lo"], hi=c["dms"]["hi"],
+                                          width_us=c["dms"]["width_us"], tol=c["dms"]["tol"])))
+    gmax, gmin = c["gulp_hi"], c["gulp_lo"]
+    host = {}
+    for band in c["bands"]:
+        nch = band["nchans"]
+        base = synth.normal_u8(c["seed"], nch, 1 << 16, nch)
+        h = torch.empty((gmax, nch), dtype=torch.uint8, pin_memory=True)
+        hn = h.numpy()
+        for r0 in range(0, gmax, 1 << 16):
+            hn[r0:r0 + (1 << 16)] = base
+        host[nch] = hn
+    free, _ = torch.cuda.mem_get_info()
+    arena = int(min(112 << 30, free * 0.6))  # room for two full 13-gulp launches
+
+    def sizes(n):
+        return [int(v) for v in rng.integers(gmin, gmax + 1, n)]
+
+    per_beam = 6
+    cap_reqs = [(b, g) for g in sizes(per_beam) for b in range(len(plans))]
+
+    def capacity(max_batch):
+        """Saturated throughput of the engine: every request queued at once."""
+        srv = dd.Server(arena_bytes=arena, max_batch=max_batch, max_inflight=2)
+        beams = [srv.add_beam(p, 8, gmax) for p in plans]
+        # warm-up: one full gulp per beam (stream images, staging tables)
+        _serve_all(srv, plans, beams, [(b, gmax) for b in range(len(plans))], host)
+        t0 = time.perf_counter()
+        res = _serve_all(srv, plans, beams, cap_reqs, host)
+        wall = time.perf_counter() - t0
+        srv.close()
+        return sum(u for _, u in res) / wall
+
+    def sequential():
+        """The same requests as plain per-beam streaming calls, one beam at a
+        time: input copy, dd_stream_push on device buffers, wait."""
+        st = torch.cuda.Stream()
+        streams = [dd.Stream(p, 8, gmax) for p in plans]
+        d_in = {n: torch.empty((gmax, n), dtype=torch.uint8, device="cuda") for n in host}
+        d_out = {b: torch.empty((p.dm_count, gmax), dtype=torch.int32, device="cuda")
+                 for b, p in enumerate(plans) if b < 2}
+
+        def one(b, g):
+            n = plans[b].nchans
+            with torch.cuda.stream(st):
+                d_in[n][:g].copy_(torch.from_numpy(host[n][:g]), non_blocking=True)
+            k = streams[b].push(d_in[n][:g], g, d_out[b % 2][:, :g], stream=st)
+            st.synchronize()
+            return float(plans[b].nchans) * plans[b].dm_count * k
+
+        for b in range(len(plans)):
+            one(b, gmax)
+        t0 = time.perf_counter()
+        units = sum(one(b, g) for b, g in cap_reqs)
+        return units / (time.perf_counter() - t0)
+
+    cap_b = capacity(13)
+    cap_1 = capacity(1)
+    cap_s = sequential()
+    # Poisson arrivals at 70 % of the batched capacity
+    n_per_beam = 10
+    mean_g = 0.5 * (gmin + gmax)
+    work = sum(float(p.nchans) * p.dm_count * mean_g for p in plans)  # units per round of gulps
+    lam = c["offered_load"] * cap_b / work                             # gulps/s per beam
+    srv = dd.Server(arena_bytes=arena, max_batch=13, max_inflight=2)
+    beams = [srv.add_beam(p, 8, gmax) for p in plans]
+    _serve_all(srv, plans, beams, [(b, gmax) for b in range(len(plans))], host)
+    reqs, t_sched = [], []
+    for b in range(len(plans)):
+        t = 0.0
+        for g in sizes(n_per_beam):
+            t += rng.exponential(1.0 / lam)
+            reqs.append((b, g))
+            t_sched.append(t)
+    t0 = time.perf_counter()
+    res = _serve_all(srv, plans, beams, reqs, host, t_sched)
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([l for l, _ in res])
+    return {
+        "workload": "serving-13beam-u8: 13 beams, 512/1024 ch by turn, 8-bit, DM 0-2000 "
+                    "(841/1434 trials), gulps U[2^16, 2^19], Poisson arrivals",
+        "offered_load": c["offered_load"],
+        "speedup_over_real_time": lam * mean_g * c["dt"],
+        "requests": len(reqs),
+        "throughput": sum(u for _, u in res) / wall / 1e9,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max())},
+        "capacity_batched": cap_b / 1e9,
+        "capacity_engine_one_beam_per_launch": cap_1 / 1e9,
+        "capacity_sequential_per_beam": cap_s / 1e9,
+        "batched_over_sequential": cap_b / cap_s,
+        "capacity_requests": len(cap_reqs),
+        "unit": UNIT,
+        "arena_gb": arena / 2**30,
+        "latency_definition": "scheduled arrival -> output ready on the GPU (host-function "
+                              "stamp behind the launch)",
+    }
+
+
 def run_ours(a, rank, world, local_rank):
     import torch
     import paper_1201_5380_gb300 as dd
@@ -319,6 +477,10 @@ def run_ours(a, rank, world, local_rank):
                      "hbm_gbs_used": hbm},
         "clocks": clocks,
     }
+    if rank == 0 and world == 1 and not a.no_serving and not a.gulp:
+        del d_in, out
+        torch.cuda.empty_cache()
+        line["serving"] = run_serving(a)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         import oracle
         oracle.build()

@@ -383,7 +383,10 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
         atomicOr(p.status, DEV_BAD_READ);
         wi = 0;
       }
-      const uint32_t words = has ? (uint32_t)min((int64_t)nwl, row_words - wi) : 0u;
+      // the words this channel's trials read (plus the next word, which the
+      // lane-shift build reads), not the launch-wide window
+      const int64_t want = min((int64_t)nwl, (int64_t)((r.y + 4 + 3) & ~3));
+      const uint32_t words = has ? (uint32_t)min(want, row_words - wi) : 0u;
       const uint32_t tab_bytes = (uint32_t)n_entries * 4u;
       const uint32_t total = __reduce_add_sync(0xffffffffu, words * 4u) + tab_bytes;
       if (lane == 0) {

@@ -236,6 +236,22 @@ void drop_stage_tabs(Plan& p, int kind_mask) {
   }
 }
 
+// Channels per chunk for a launch whose largest staging spread is `spread`:
+// a power of two, at most two address-table entries per thread, and both
+// staging buffers within the shared-memory budget (0 if nothing fits).
+int chunk_channels(const Plan& p, int fmt, int32_t spread) {
+  const int cfg = tile_cfg_index(p.tune);
+  const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
+  const int nww = window_words(fmt, p.tune, spread);
+  const int nt = kTileCfgs[cfg].nwarp * 32;
+  int cc = 4;
+  while (cc * 2 <= p.tune.chans_per_chunk) cc *= 2;
+  const size_t smem_cap = 220 * 1024;
+  while (cc > 4 && (dedisp_smem_bytes(fmt, cfg, cc, nww) > smem_cap || B * cc > 2 * nt)) cc /= 2;
+  if (dedisp_smem_bytes(fmt, cfg, cc, nww) > smem_cap || B * cc > 2 * nt) return 0;
+  return cc;
+}
+
 // Fill launch parameters for a set of segments sharing one staged format.
 static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector<SegSpec>& specs,
                                bool vec_out, LaunchPlan* L) {
@@ -249,15 +265,8 @@ static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector
     nchan_max = std::max(nchan_max, (int)s.seg.nchan);
   }
   const int nww = window_words(fmt, p.tune, spread);
-  // channels per chunk: a power of two, at most two address-table entries
-  // per thread, and both staging buffers within the shared-memory budget
-  const int nt = kTileCfgs[cfg].nwarp * 32;
-  int cc = 4;
-  while (cc * 2 <= p.tune.chans_per_chunk) cc *= 2;
-  const size_t smem_cap = 220 * 1024;
-  while (cc > 4 && (dedisp_smem_bytes(fmt, cfg, cc, nww) > smem_cap || B * cc > 2 * nt)) cc /= 2;
-  if (dedisp_smem_bytes(fmt, cfg, cc, nww) > smem_cap || B * cc > 2 * nt)
-    return DD_ERR_INVALID_ARG;
+  const int cc = chunk_channels(p, fmt, spread);
+  if (cc == 0) return DD_ERR_INVALID_ARG;
 
   L->fmt = fmt;
   L->outk = outk;

@@ -287,6 +287,9 @@ void make_blocks(const int32_t* delays, int ndm, int nchans, int stride, int B,
 // 220 KB of shared memory.
 constexpr int32_t kSpreadBudget = 4400;
 int time_tile(int fmt, const Tuning& t);
+// Channels per staged chunk that plan p's tiling gives a launch whose
+// largest staging spread is `spread` (0 if it cannot be staged).
+int chunk_channels(const Plan& p, int fmt, int32_t spread);
 dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
                              const std::vector<DirectJob>& jobs, LaunchPlan* lpl,
                              std::vector<StageTab*>* tabs = nullptr);
