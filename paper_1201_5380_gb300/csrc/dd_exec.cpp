@@ -465,6 +465,84 @@ static dd_status exec_direct(Plan& p, const ExecArgs& a, int fmt) {
   return run_launch(p, L, a.st);
 }
 
+// Direct transform into host memory: the trial blocks run as kOutParts
+// launches, and each part's output rows are copied to the host on a second
+// stream while the next part computes (the copy-out of a 2.5 GB survey
+// output otherwise adds half the kernel time).  Synchronises.
+static dd_status exec_direct_host_out(Plan& p, const ExecArgs& a, int fmt, void* host_out) {
+  constexpr int kOutParts = 4;
+  dd_status s = ensure_device_tables(p);
+  if (s != DD_OK) return s;
+  const int64_t rows = a.nsamps_out + p.max_delay;
+  DirectJob j;
+  if ((s = stage_direct_image(p, a.in, a.in_nbits, a.in_row_stride, rows, a.nsamps_out,
+                              p.d_image, a.st, &j)) != DD_OK)
+    return s;
+  j.out = a.out;
+  j.out_stride = a.out_stride;
+  LaunchPlan L;
+  if ((s = plan_direct_launch(p, fmt, fmt == FMT_F32 ? OUT_F32 : OUT_U32,
+                              vmax_for_nbits(a.in_nbits), {j}, &L)) != DD_OK)
+    return s;
+  cudaError_t e = cudaSuccess;
+  if (!p.copy_st) e = cudaStreamCreateWithFlags(&p.copy_st, cudaStreamNonBlocking);
+  while (e == cudaSuccess && p.part_ev.size() < (size_t)kOutParts) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) p.part_ev.push_back(ev);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  const Seg g = L.lp.segs[0];
+  const std::vector<int32_t>& starts = p.blocks_B[b_index(kTileCfgs[L.cfg].nwarp *
+                                                          kTileCfgs[L.cfg].dpw)];
+  const int nblk = g.n_dmblk;
+  const int64_t nchunks = (g.nchan + L.lp.cc - 1) / L.lp.cc;
+  const int64_t per_blk = nchunks * kTileCfgs[L.cfg].nwarp * kTileCfgs[L.cfg].dpw * L.lp.cc;
+  const int64_t tiles = (g.nsamps + time_tile(fmt, p.tune) - 1) / time_tile(fmt, p.tune);
+  const int parts = std::min(kOutParts, nblk);
+  auto bounds = [&](int q, int* b0, int* b1) {
+    *b0 = (int)((int64_t)nblk * q / parts);
+    *b1 = (int)((int64_t)nblk * (q + 1) / parts);
+  };
+  // every launch first (a copy into pageable memory blocks the host), then
+  // the copies, each behind its part's event
+  for (int q = 0; q < parts; ++q) {
+    int b0, b1;
+    bounds(q, &b0, &b1);
+    if (b1 <= b0) continue;
+    LaunchPlan Lq = L;
+    Seg& sq = Lq.lp.segs[0];
+    sq.blk = g.blk + b0;
+    sq.n_dmblk = b1 - b0;
+    sq.atab = g.atab + b0 * per_blk;
+    sq.crec = g.crec + (int64_t)b0 * g.nchan * 2;
+    sq.item_begin = 0;
+    Lq.lp.n_items = (int64_t)(b1 - b0) * tiles;
+    Lq.grid = (int)std::min<int64_t>(L.grid, Lq.lp.n_items);
+    if ((s = run_launch(p, Lq, a.st)) != DD_OK) return s;
+    if ((e = cudaEventRecord(p.part_ev[q], a.st)) != cudaSuccess) return cuda_status(e);
+  }
+  for (int q = 0; q < parts; ++q) {
+    int b0, b1;
+    bounds(q, &b0, &b1);
+    if (b1 <= b0) continue;
+    // rows of trials [starts[b0], starts[b1]) are final: copy them out
+    // (row by row pitch: the caller's padding past nsamps is not written)
+    const int64_t d0 = starts[b0], d1 = starts[b1];
+    const size_t off = (size_t)(d0 * a.out_stride) * 4;
+    const size_t pitch = (size_t)a.out_stride * 4;
+    if ((e = cudaStreamWaitEvent(p.copy_st, p.part_ev[q], 0)) != cudaSuccess ||
+        (e = cudaMemcpy2DAsync(static_cast<uint8_t*>(host_out) + off, pitch,
+                               static_cast<const uint8_t*>(a.out) + off, pitch,
+                               (size_t)a.nsamps_out * 4, (size_t)(d1 - d0),
+                               cudaMemcpyDeviceToHost, p.copy_st)) != cudaSuccess)
+      return cuda_status(e);
+  }
+  if ((e = cudaStreamSynchronize(a.st)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaStreamSynchronize(p.copy_st)) != cudaSuccess) return cuda_status(e);
+  return DD_OK;
+}
+
 static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
   if (fmt == FMT_F32) return DD_ERR_UNSUPPORTED_NBITS;
   dd_status s = upload_subband(p);
@@ -641,10 +719,12 @@ extern "C" dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void* in
     return cuda_status(e);
   a.in = p->d_in.p;
   a.out = p->d_out.p;
+  if (!sub) return exec_direct_host_out(*p, a, fmt, out);
   dd_status s = exec_device(*p, a);
   if (s != DD_OK) return s;
-  if ((e = cudaMemcpyAsync(out, p->d_out.p, out_bytes, cudaMemcpyDeviceToHost, a.st)) !=
-      cudaSuccess)
+  if ((e = cudaMemcpy2DAsync(out, (size_t)out_stride * 4, p->d_out.p, (size_t)out_stride * 4,
+                             (size_t)nsamps_out * 4, (size_t)ndm(*p), cudaMemcpyDeviceToHost,
+                             a.st)) != cudaSuccess)
     return cuda_status(e);
   if ((e = cudaStreamSynchronize(a.st)) != cudaSuccess) return cuda_status(e);
   return DD_OK;

@@ -208,6 +208,9 @@ struct Plan {
   std::vector<TimedLaunch> timed;
   double timed_ms[2] = {0.0, 0.0};
   int64_t timed_n[2] = {0, 0};
+  // host-pointer execute: output copies overlap the next part's compute
+  cudaStream_t copy_st = nullptr;
+  std::vector<cudaEvent_t> part_ev;
   std::mutex mu;
   ~Plan();
 };

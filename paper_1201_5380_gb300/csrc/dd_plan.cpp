@@ -56,7 +56,11 @@ static void drain_timing(Plan& p) {
   cudaGetLastError();
 }
 
-Plan::~Plan() { drain_timing(*this); }
+Plan::~Plan() {
+  drain_timing(*this);
+  for (cudaEvent_t e : part_ev) cudaEventDestroy(e);
+  if (copy_st) cudaStreamDestroy(copy_st);
+}
 
 KernelTimer::KernelTimer(Plan* plan, int k, cudaStream_t s) : p(plan), kind(k), st(s) {
   if (!p || !p->timing) return;

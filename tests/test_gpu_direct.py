@@ -124,6 +124,21 @@ def test_host_pointer_path(orc):
     assert np.array_equal(out, orc.direct(x, 2, 1024, nsamps, odelays(orc, plan)))
 
 
+def test_host_pointer_path_in_parts_with_padded_rows(orc):
+    """The host-output path runs the trial blocks in several launches and
+    copies each part out while the next computes: every row, padded stride."""
+    torch_cuda()
+    plan = _survey_plan(step=6)       # ~200 trials: several trial blocks per part
+    nsamps = 1300
+    rows = nsamps + plan.max_delay
+    x = synth.uniform_packed(19, 0, rows, 1024, 2)
+    out = np.full((plan.dm_count, nsamps + 37), 0xDEADBEEF, np.uint32)
+    plan.execute(x, 2, nsamps, out)
+    ref = orc.direct(x, 2, 1024, nsamps, odelays(orc, plan))
+    assert np.array_equal(out[:, :nsamps], ref)
+    assert np.all(out[:, nsamps:] == 0xDEADBEEF)
+
+
 @pytest.mark.parametrize("tiling", [(32, 4, 4), (32, 8, 4), (32, 16, 4), (64, 8, 2), (64, 4, 2),
                                     (16, 4, 4), (16, 8, 4)])
 def test_every_tiling_bit_exact(orc, tiling):
