@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-subband", action="store_true")
     ap.add_argument("--gulp", type=int, default=0,
                     help="samples per gulp (default: the workload's 2^19); smaller values "
                          "are for profiler captures, not bench lines")
@@ -361,6 +362,91 @@ def run_serving(a):
     }
 
 
+def _boxcar_snr(row, t0):
+    """Best peak S/N over boxcar widths 1..256 (a pulse search's matched
+    filter) near t0 in one dedispersed series, each width against its own
+    mean and spread away from the pulse.  Returns (S/N, width)."""
+    r = row.astype(np.float64)
+    c = np.concatenate([[0.0], np.cumsum(r)])
+    best = (-np.inf, 0)
+    for width in (1, 2, 4, 8, 16, 32, 64, 128, 256):
+        box = c[width:] - c[:-width]
+        lo, hi = max(0, t0 - 512), min(box.size, t0 + 512)
+        off = np.concatenate([box[:max(0, t0 - 8192)], box[t0 + 8192:]])
+        snr = (box[lo:hi].max() - off.mean()) / off.std()
+        best = max(best, (snr, width))
+    return best
+
+
+def run_subband(a, x, plan_direct, d_out_direct, G):
+    """Sub-band dedispersion (Sec. 4) on the survey band with N'_nu = N'_DM
+    = 32: throughput in direct-equivalent units and the peak-S/N loss on the
+    injected pulses against direct, beside the App. B smearing bound."""
+    import torch
+    import paper_1201_5380_gb300 as dd
+
+    c, sb = configs.SURVEY, configs.SUBBAND
+    n_sub, n_dm = sb["chans_per_subband"], sb["dms_per_nominal"]
+    plan = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0),
+                   subband=(n_sub, n_dm))
+    rows = G + max(plan.max_delay, plan.subband_max_delay)
+    if x.shape[0] < rows:
+        x = np.concatenate([x, np.zeros((rows - x.shape[0], x.shape[1]), x.dtype)])
+    d_in = torch.from_numpy(np.ascontiguousarray(x[:rows])).cuda()
+    out = torch.empty((plan.dm_count, G), dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        plan.execute(d_in, 2, G, out, subband=True)
+    torch.cuda.synchronize()
+    plan.reset_kernel_timing()
+    plan.set_kernel_timing(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    reps = 5
+    ev[0].record()
+    for _ in range(reps):
+        plan.execute(d_in, 2, G, out, subband=True)
+    ev[1].record()
+    torch.cuda.synchronize()
+    plan.set_kernel_timing(False)
+    if plan.device_status() != 0:
+        raise RuntimeError("device-side bound flag set in the sub-band run")
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    k_ms, k_n = plan.kernel_timing(1)
+    units = float(c["nchans"]) * plan.dm_count * G
+    adds = G * (c["nchans"] * -(-plan.dm_count // n_dm) + plan.dm_count * (c["nchans"] // n_sub))
+    dms = plan.dms
+
+    def inv_f2(chan):  # App. B: the band edge below channel `chan`, MHz^-2
+        return 1.0 / (c["f0"] + chan * c["df"]) ** 2
+
+    snr = []
+    for p in c["pulses"]:
+        k = int(np.argmin(np.abs(dms - p["dm"])))
+        g0 = (k // n_dm) * n_dm
+        g1 = min(g0 + n_dm, plan.dm_count) - 1
+        # App. B: smearing of the lowest sub-band over the group's DM span,
+        # and the relative smearing mu = sqrt(W^2 + t_SB^2) / W
+        t_sb = (dms[g1] - dms[g0]) * 4.148808e3 * (inv_f2(c["nchans"]) -
+                                                  inv_f2(c["nchans"] - n_sub))
+        w = p["width"] * c["dt"]
+        mu = float(np.sqrt(w * w + t_sb * t_sb) / w)
+        s_d, w_d = _boxcar_snr(d_out_direct[k].cpu().numpy().view(np.uint32), p["t0"])
+        s_s, w_s = _boxcar_snr(out[k].cpu().numpy().view(np.uint32), p["t0"])
+        snr.append({"dm": float(dms[k]), "snr_direct": s_d, "width_direct": w_d,
+                    "snr_subband": s_s, "width_subband": w_s, "ratio": s_s / s_d,
+                    "app_b_mu": mu, "app_b_ratio": mu ** -0.5})
+    return {
+        "workload": "subband-1024ch-u2-32x32: the survey gulp, 32 sub-bands of 32 channels, "
+                    "32 trials per nominal DM",
+        "ms_per_step": ms, "kernels_ms": k_ms / reps,
+        "value": units / (ms / 1e3) / 1e9, "unit": UNIT + " (direct-equivalent)",
+        "adds_per_step": adds, "adds_vs_direct": adds / units,
+        "snr_loss": snr,
+        "snr_note": "best boxcar (1..256 samples) peak S/N at each injected pulse's trial; "
+                    "app_b_ratio = mu^-1/2 (matched-filter loss for the smeared width) with "
+                    "mu from the App. B bound over the trial group's DM span",
+    }
+
+
 def run_ours(a, rank, world, local_rank):
     import torch
     import paper_1201_5380_gb300 as dd
@@ -477,6 +563,9 @@ def run_ours(a, rank, world, local_rank):
                      "hbm_gbs_used": hbm},
         "clocks": clocks,
     }
+    if rank == 0 and world == 1 and not a.no_subband and not a.gulp:
+        line["subband"] = run_subband(a, x, plan, out, G)
+        line["subband"]["speedup_vs_direct_kernels"] = k_ms / line["subband"]["kernels_ms"]
     if rank == 0 and world == 1 and not a.no_serving and not a.gulp:
         del d_in, out
         torch.cuda.empty_cache()
