@@ -447,6 +447,20 @@ def run_subband(a, x, plan_direct, d_out_direct, G):
     }
 
 
+def replica_throughput(local_ms, units_per_rank, world, device):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units in local_ms: the slowest rank's time (max over
+    ranks) and world * units / that time, in G units/s.  Ranks do not
+    exchange data; this reduction is the only collective."""
+    import torch
+    t_ms = float(local_ms)
+    if world > 1:
+        t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+    return t_ms, world * units_per_rank / (t_ms / 1e3) / 1e9
+
+
 def run_ours(a, rank, world, local_rank):
     import torch
     import paper_1201_5380_gb300 as dd
@@ -498,13 +512,9 @@ def run_ours(a, rank, world, local_rank):
     ct_ms, ct_n = plan.kernel_timing(0)
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_step = total_ms / a.steps
     units = float(nchans) * ndm * G
-    value = world * units * a.steps / (total_ms / 1e3) / 1e9
+    total_ms, value = replica_throughput(total_ms, units * a.steps, world, dev)
+    ms_step = total_ms / a.steps
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     h_in = torch.empty(x.shape, dtype=torch.uint8, pin_memory=True)
@@ -517,11 +527,8 @@ def run_ours(a, rank, world, local_rank):
     for _ in range(a.e2e_steps):
         plan.execute(hin, 2, G, hout)
     e2e_s = (time.perf_counter() - t0) / max(a.e2e_steps, 1)
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * units / e2e_s / 1e9
+    e2e_ms, e2e_value = replica_throughput(e2e_s * 1e3, units, world, dev)
+    e2e_s = e2e_ms / 1e3
     if not np.array_equal(hout.view(np.uint32)[:, :64],
                           out[:, :64].cpu().numpy().view(np.uint32)):
         raise RuntimeError("host-path output differs from device-path output")

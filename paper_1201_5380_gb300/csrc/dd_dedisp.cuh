@@ -588,6 +588,7 @@ cudaError_t dispatch_cfg(int cfg, const LaunchParams* p, int grid, size_t smem,
     DD_CFG_CASE(0)
     DD_CFG_CASE(1)
     DD_CFG_CASE(2)
+    DD_CFG_CASE(3)
 #undef DD_CFG_CASE
     default:
       return cudaErrorInvalidValue;

@@ -104,8 +104,8 @@ struct LaunchParams {
 struct TileCfg {
   int nwarp, dpw, k;  // warps per block, trials per warp, words per lane
 };
-constexpr TileCfg kTileCfgs[] = {{16, 2, 4}, {16, 4, 2}, {8, 2, 4}};
-constexpr int kNumTileCfgs = 3;
+constexpr TileCfg kTileCfgs[] = {{16, 2, 4}, {16, 4, 2}, {8, 2, 4}, {8, 4, 2}};
+constexpr int kNumTileCfgs = 4;
 
 // Host launchers (dd_kernels_*.cu).
 cudaError_t launch_dedisp(int fmt, int outk, bool wide, int cfg, const LaunchParams& p,
