@@ -129,8 +129,12 @@ dd_status dd_plan_set_subband(dd_plan plan, int chans_per_subband,
                               int dms_per_nominal);
 
 /* Kernel tiling: trials per thread block (16, 32 or 64), channels staged
- * per pass (4, 8, 16 or 32) and output words per lane (2 or 4);
- * 0 selects the built-in default for each.  The autotuner below sets these. */
+ * per pass (4, 8, 16 or 32) and output words per lane (2, 4 or 8; compiled
+ * shapes: 32x4, 64x2, 16x4, 32x2, 32x8 trials x words).  0 keeps the current
+ * value.  words_per_lane < 0 (the default) picks it per input format: 8 for
+ * 8-bit and float input (16- and 32-bit lanes), 4 for 1/2/4-bit input.
+ * The autotuner below sets all three.  dd_plan_get_tuning reports 0 words
+ * per lane while it is chosen per format. */
 dd_status dd_plan_set_tuning(dd_plan plan, int dms_per_block, int chans_per_chunk,
                              int words_per_lane);
 dd_status dd_plan_get_tuning(dd_plan plan, int *dms_per_block, int *chans_per_chunk,

@@ -326,7 +326,19 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
 
   uint32_t kk = 0;  // chunks consumed by this block (buffer = kk & 1, parity = (kk >> 1) & 1)
 
-  for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+  // next work item: from the launch's counter (neighbouring items run
+  // together), else the static grid stride
+  __shared__ long long s_next_item;
+  auto next_item = [&](int64_t cur) -> int64_t {
+    if (!p.next_item) return cur + gridDim.x;
+    __syncthreads();  // every thread has read the previous value
+    if (tid == 0)
+      s_next_item = (long long)gridDim.x + (long long)atomicAdd(p.next_item, 1ull);
+    __syncthreads();
+    return s_next_item;
+  };
+
+  for (int64_t item = blockIdx.x; item < p.n_items; item = next_item(item)) {
     const Seg& S = p.segs[find_seg(p, item)];
     const int64_t li = item - S.item_begin;
     const int n_dmblk = S.n_dmblk;
@@ -589,6 +601,7 @@ cudaError_t dispatch_cfg(int cfg, const LaunchParams* p, int grid, size_t smem,
     DD_CFG_CASE(1)
     DD_CFG_CASE(2)
     DD_CFG_CASE(3)
+    DD_CFG_CASE(4)
 #undef DD_CFG_CASE
     default:
       return cudaErrorInvalidValue;

@@ -240,9 +240,9 @@ void drop_stage_tabs(Plan& p, int kind_mask) {
 // a power of two, at most two address-table entries per thread, and both
 // staging buffers within the shared-memory budget (0 if nothing fits).
 int chunk_channels(const Plan& p, int fmt, int32_t spread) {
-  const int cfg = tile_cfg_index(p.tune);
+  const int cfg = tile_cfg_index(tuning_for(p.tune, fmt));
   const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
-  const int nww = window_words(fmt, p.tune, spread);
+  const int nww = window_words(fmt, tuning_for(p.tune, fmt), spread);
   const int nt = kTileCfgs[cfg].nwarp * 32;
   int cc = 4;
   while (cc * 2 <= p.tune.chans_per_chunk) cc *= 2;
@@ -255,16 +255,16 @@ int chunk_channels(const Plan& p, int fmt, int32_t spread) {
 // Fill launch parameters for a set of segments sharing one staged format.
 static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector<SegSpec>& specs,
                                bool vec_out, LaunchPlan* L) {
-  const int cfg = tile_cfg_index(p.tune);
+  const int cfg = tile_cfg_index(tuning_for(p.tune, fmt));
   const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
-  const int T = time_tile(fmt, p.tune);
+  const int T = time_tile(fmt, tuning_for(p.tune, fmt));
   int32_t spread = 0;
   int nchan_max = 0;
   for (auto& s : specs) {
     spread = std::max(spread, s.spread);
     nchan_max = std::max(nchan_max, (int)s.seg.nchan);
   }
-  const int nww = window_words(fmt, p.tune, spread);
+  const int nww = window_words(fmt, tuning_for(p.tune, fmt), spread);
   const int cc = chunk_channels(p, fmt, spread);
   if (cc == 0) return DD_ERR_INVALID_ARG;
 
@@ -334,6 +334,10 @@ static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector
 dd_status run_launch(Plan& p, LaunchPlan& L, cudaStream_t st) {
   if (L.lp.n_items == 0) return DD_OK;
   L.lp.status = static_cast<uint32_t*>(p.d_status.p);
+  L.lp.next_item = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(p.d_status.p) + 8 +
+                                                         8 * (p.launch_seq++ % kItemCounters));
+  cudaError_t e0 = cudaMemsetAsync(L.lp.next_item, 0, 8, st);
+  if (e0 != cudaSuccess) return cuda_status(e0);
   KernelTimer kt(&p, 1, st);
   return cuda_status(launch_dedisp(L.fmt, L.outk, L.wide, L.cfg, L.lp, L.grid, L.smem, st));
 }
@@ -341,7 +345,7 @@ dd_status run_launch(Plan& p, LaunchPlan& L, cudaStream_t st) {
 dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
                              const std::vector<DirectJob>& jobs, LaunchPlan* L,
                              std::vector<StageTab*>* tabs) {
-  const int cfg = tile_cfg_index(p.tune);
+  const int cfg = tile_cfg_index(tuning_for(p.tune, fmt));
   const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
   std::vector<SegSpec> specs;
   bool vec = true;
@@ -498,7 +502,7 @@ static dd_status exec_direct_host_out(Plan& p, const ExecArgs& a, int fmt, void*
   const int nblk = g.n_dmblk;
   const int64_t nchunks = (g.nchan + L.lp.cc - 1) / L.lp.cc;
   const int64_t per_blk = nchunks * kTileCfgs[L.cfg].nwarp * kTileCfgs[L.cfg].dpw * L.lp.cc;
-  const int64_t tiles = (g.nsamps + time_tile(fmt, p.tune) - 1) / time_tile(fmt, p.tune);
+  const int64_t tiles = (g.nsamps + time_tile(fmt, tuning_for(p.tune, fmt)) - 1) / time_tile(fmt, tuning_for(p.tune, fmt));
   const int parts = std::min(kOutParts, nblk);
   auto bounds = [&](int q, int* b0, int* b1) {
     *b0 = (int)((int64_t)nblk * q / parts);
@@ -550,7 +554,7 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
   const int C = p.nchans, Np = p.sb_chans, nsb = C / Np;
   const int n = ndm(p);
   const int ng = (n + p.sb_dms - 1) / p.sb_dms;
-  const int cfg = tile_cfg_index(p.tune);
+  const int cfg = tile_cfg_index(tuning_for(p.tune, fmt));
   const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
   const int vmax_in = vmax_for_nbits(a.in_nbits);
   const int64_t G = a.nsamps_out;
@@ -561,7 +565,7 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
   const int32_t spread1 = p.sb1_spread_B[bi], lo1 = p.sb1_lo_B[bi];
   const int32_t maxrel = p.sb_maxrel;
   if (lo1 > kPad) return DD_ERR_INVALID_ARG;
-  const int64_t rw = image_row_words(fmt, p.tune, len1, maxrel, spread1);
+  const int64_t rw = image_row_words(fmt, tuning_for(p.tune, fmt), len1, maxrel, spread1);
   cudaError_t e = p.d_image.ensure((size_t)C * rw * 4);
   if (e != cudaSuccess) return cuda_status(e);
   uint32_t* img = static_cast<uint32_t*>(p.d_image.p);
@@ -579,9 +583,9 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
   const int fmt2 = half ? FMT_HALF : FMT_U32;
   const int32_t spread2 = p.sb2_spread_B[bi], lo2 = p.sb2_lo_B[bi];
   if (lo2 > kPad) return DD_ERR_INVALID_ARG;
-  const int T1 = time_tile(fmt, p.tune);
+  const int T1 = time_tile(fmt, tuning_for(p.tune, fmt));
   const int spw2 = fmt_spw(fmt2);
-  int64_t rw2 = image_row_words(fmt2, p.tune, G, (int32_t)p.sb_len1_extra, spread2);
+  int64_t rw2 = image_row_words(fmt2, tuning_for(p.tune, fmt2), G, (int32_t)p.sb_len1_extra, spread2);
   const int64_t st1_words = (kPad + ((len1 + T1 - 1) / T1) * T1) / spw2 + 8;
   rw2 = std::max(rw2, (st1_words + 31) & ~(int64_t)31);
   const size_t s_bytes = (size_t)ng * nsb * rw2 * 4;

@@ -96,16 +96,30 @@ struct LaunchParams {
   int32_t f0, f1, f2;  // flush periods (groups of 4 channels) per level
   int64_t n_items;
   uint32_t* status;
+  // work-item counter (zeroed before the launch): blocks take their next
+  // item from it, so the blocks running at any moment work on neighbouring
+  // items (and share the staged windows of a tile in L2) however long the
+  // launch; null = static striding by the grid size
+  unsigned long long* next_item;
   int32_t vec_out;   // 1 if every output row/tile start is 16-byte aligned
   int32_t pad_;
 };
+
+// The plan's status buffer: the status word, then kItemCounters launch
+// counters taken round-robin, so launches of one plan that overlap on
+// different streams do not share a counter.
+constexpr int kItemCounters = 32;
+constexpr size_t kStatusBytes = 8 + 8 * kItemCounters;
 
 // Kernel shapes compiled into the library.
 struct TileCfg {
   int nwarp, dpw, k;  // warps per block, trials per warp, words per lane
 };
-constexpr TileCfg kTileCfgs[] = {{16, 2, 4}, {16, 4, 2}, {8, 2, 4}, {8, 4, 2}};
-constexpr int kNumTileCfgs = 4;
+// (16, 2, 8) is for the narrow-accumulator formats (8-bit and wider input,
+// where a wide window over a short tile makes staging dominate); the 4- and
+// 8-bit-lane formats compile it too but spill.
+constexpr TileCfg kTileCfgs[] = {{16, 2, 4}, {16, 4, 2}, {8, 2, 4}, {8, 4, 2}, {16, 2, 8}};
+constexpr int kNumTileCfgs = 5;
 
 // Host launchers (dd_kernels_*.cu).
 cudaError_t launch_dedisp(int fmt, int outk, bool wide, int cfg, const LaunchParams& p,
@@ -135,7 +149,7 @@ struct DevBuf {
 struct Tuning {
   int dms_per_block = 32;
   int chans_per_chunk = 8;
-  int words_per_lane = 4;
+  int words_per_lane = 0;  // 0: chosen per input format (tuning_for)
 };
 
 // Staging tables of one delay table for one launch geometry.  They do not
@@ -211,6 +225,7 @@ struct Plan {
   // host-pointer execute: output copies overlap the next part's compute
   cudaStream_t copy_st = nullptr;
   std::vector<cudaEvent_t> part_ev;
+  uint32_t launch_seq = 0;  // round-robin index into the item counters
   std::mutex mu;
   ~Plan();
 };
@@ -232,6 +247,11 @@ dd_status ensure_device_tables(Plan& p);
 dd_status prepare_subband(Plan& p);  // host tables only
 dd_status upload_subband(Plan& p);   // host tables + device copies
 int tile_cfg_index(const Tuning& t);
+// The tuning a launch of staged format fmt uses: words per lane 0 resolves
+// to 8 for the narrow-accumulator formats (16- and 32-bit lanes: 8-bit and
+// float input, the sub-band intermediate) and 4 otherwise, when a compiled
+// tile shape has that many trials per block and words per lane.
+Tuning tuning_for(const Tuning& t, int fmt);
 
 // Direct and sub-band execution on device buffers (asynchronous on st).
 struct ExecArgs {
@@ -288,7 +308,7 @@ void make_blocks(const int32_t* delays, int ndm, int nchans, int stride, int B,
 // Largest staging spread (samples) of a trial block: with double-buffered
 // staging and 4-channel chunks the windows of every format then fit in
 // 220 KB of shared memory.
-constexpr int32_t kSpreadBudget = 4400;
+constexpr int32_t kSpreadBudget = 4000;
 int time_tile(int fmt, const Tuning& t);
 // Channels per staged chunk that plan p's tiling gives a launch whose
 // largest staging spread is `spread` (0 if it cannot be staged).

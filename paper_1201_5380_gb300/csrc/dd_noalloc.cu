@@ -68,11 +68,11 @@ extern "C" dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const 
 
   // Plan the launch first, with the staging tables left on the host: they
   // size the scratch.  Device pointers are patched in once it is laid out.
-  const int cfg = tile_cfg_index(p->tune);
+  const int cfg = tile_cfg_index(tuning_for(p->tune, fmt));
   const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
   const int bi = b_index(B);
   const std::vector<int32_t>& blocks = p->blocks_B[bi];
-  const int64_t rw = image_row_words(fmt, p->tune, nsamps_out, p->max_delay, p->spread_B[bi]);
+  const int64_t rw = image_row_words(fmt, tuning_for(p->tune, fmt), nsamps_out, p->max_delay, p->spread_B[bi]);
   DirectJob j;
   j.img = reinterpret_cast<const uint32_t*>(sc);
   j.row_words = rw;
@@ -113,7 +113,7 @@ extern "C" dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const 
 
   // The array keeps the previous call's contents: reset the status word and
   // reload the tables (the image is fully rewritten by the corner turn).
-  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(uint32_t), st);
+  cudaError_t e = cudaMemsetAsync(status, 0, 16, st);  // status word and item counter
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(mask, p->mask.data(), (size_t)p->nchans, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -138,5 +138,6 @@ extern "C" dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const 
   g.atab = atab;
   g.crec = crec;
   L.lp.status = status;
+  L.lp.next_item = reinterpret_cast<unsigned long long*>(sc + off_status + 8);
   return cuda_status(launch_dedisp(L.fmt, L.outk, L.wide, L.cfg, L.lp, L.grid, L.smem, st));
 }

@@ -152,8 +152,8 @@ dd_status ensure_device_tables(Plan& p) {
     p.blk_dirty = false;
   }
   if (!p.d_status.p) {
-    if ((e = p.d_status.ensure(sizeof(uint32_t))) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaMemset(p.d_status.p, 0, sizeof(uint32_t))) != cudaSuccess)
+    if ((e = p.d_status.ensure(kStatusBytes)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemset(p.d_status.p, 0, kStatusBytes)) != cudaSuccess)
       return cuda_status(e);
   }
   return DD_OK;
@@ -279,7 +279,29 @@ dd_status upload_subband(Plan& p) {
   return DD_OK;
 }
 
-int tile_cfg_index(const Tuning& t) {
+static bool have_cfg(int B, int K) {
+  for (int i = 0; i < kNumTileCfgs; ++i)
+    if (kTileCfgs[i].nwarp * kTileCfgs[i].dpw == B && kTileCfgs[i].k == K) return true;
+  return false;
+}
+
+Tuning tuning_for(const Tuning& t, int fmt) {
+  if (t.words_per_lane > 0) return t;
+  Tuning r = t;
+  const bool narrow = fmt == FMT_HALF || fmt == FMT_U32 || fmt == FMT_F32;
+  const int prefs[3] = {narrow ? 8 : 4, 4, 2};
+  for (int k : prefs)
+    if (have_cfg(t.dms_per_block, k)) {
+      r.words_per_lane = k;
+      return r;
+    }
+  r.words_per_lane = kTileCfgs[0].k;
+  r.dms_per_block = kTileCfgs[0].nwarp * kTileCfgs[0].dpw;
+  return r;
+}
+
+int tile_cfg_index(const Tuning& t0) {
+  const Tuning t = t0.words_per_lane > 0 ? t0 : tuning_for(t0, FMT_NIB);
   for (int i = 0; i < kNumTileCfgs; ++i) {
     const TileCfg& c = kTileCfgs[i];
     if (c.nwarp * c.dpw == t.dms_per_block && c.k == t.words_per_lane) return i;
@@ -420,14 +442,15 @@ dd_status dd_plan_set_tuning(dd_plan plan, int dms_per_block, int cc, int words)
   Tuning t = p->tune;
   if (dms_per_block) t.dms_per_block = dms_per_block;
   if (cc) t.chans_per_chunk = cc;
-  if (words) t.words_per_lane = words;
+  if (words > 0) t.words_per_lane = words;
+  if (words < 0) t.words_per_lane = 0;  // per input format
   if (t.chans_per_chunk < 4 || t.chans_per_chunk > 32 ||
       (t.chans_per_chunk & (t.chans_per_chunk - 1)))
     return DD_ERR_INVALID_ARG;
   bool found = false;
   for (int i = 0; i < kNumTileCfgs; ++i)
     if (kTileCfgs[i].nwarp * kTileCfgs[i].dpw == t.dms_per_block &&
-        kTileCfgs[i].k == t.words_per_lane)
+        (t.words_per_lane == 0 || kTileCfgs[i].k == t.words_per_lane))
       found = true;
   if (!found) return DD_ERR_INVALID_ARG;
   p->tune = t;

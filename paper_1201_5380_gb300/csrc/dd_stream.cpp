@@ -293,8 +293,8 @@ dd_status dd_batch_launch(dd_batch b, void* cuda_stream, int64_t* nsamps_out) {
   // serving workload, interleaving 512- and 1024-channel beams made the
   // launch 13-26 % slower than the same beams grouped.
   {
-    const int bi = b_index(kTileCfgs[tile_cfg_index(p0.tune)].nwarp *
-                           kTileCfgs[tile_cfg_index(p0.tune)].dpw);
+    const int c0 = tile_cfg_index(tuning_for(p0.tune, fmt));
+    const int bi = b_index(kTileCfgs[c0].nwarp * kTileCfgs[c0].dpw);
     struct Key {
       int cc, nchans, ndm;
       size_t job;
