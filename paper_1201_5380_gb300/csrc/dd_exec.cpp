@@ -474,7 +474,7 @@ static dd_status exec_direct(Plan& p, const ExecArgs& a, int fmt) {
 // stream while the next part computes (the copy-out of a 2.5 GB survey
 // output otherwise adds half the kernel time).  Synchronises.
 static dd_status exec_direct_host_out(Plan& p, const ExecArgs& a, int fmt, void* host_out) {
-  constexpr int kOutParts = 4;
+  constexpr int kOutParts = 8;
   dd_status s = ensure_device_tables(p);
   if (s != DD_OK) return s;
   const int64_t rows = a.nsamps_out + p.max_delay;
