@@ -71,12 +71,14 @@ def _load():
                                                      ctypes.c_int, P, P, P, P]),
             "orc_subband_len1": (i64, [P, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, i64]),
+            "orc_subband_nominal": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int, ctypes.c_int]),
             "orc_subband_max_delay": (i32, [P, ctypes.c_int, ctypes.c_int,
-                                            ctypes.c_int, ctypes.c_int]),
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_int]),
             "orc_subband_stage1": (ctypes.c_int, [P, ctypes.c_int, i64,
                                                   ctypes.c_int, ctypes.c_int,
-                                                  ctypes.c_int, P, ctypes.c_int,
-                                                  P, i64, i64, P]),
+                                                  ctypes.c_int, ctypes.c_int, P,
+                                                  ctypes.c_int, P, i64, i64, P]),
             "orc_subband_stage2": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int,
                                                   ctypes.c_int, P, ctypes.c_int,
                                                   i64, i64, P, i64]),
@@ -219,15 +221,20 @@ def subband_len1(delays, chans_per_sb, nsamps) -> int:
     return int(_load().orc_subband_len1(_ptr(delays), ndm, nchans, chans_per_sb, nsamps))
 
 
-def subband_max_delay(delays, chans_per_sb, ndm_per_nom) -> int:
+def subband_nominal(g, ndm, ndm_per_nom, centred=False) -> int:
+    """Nominal trial of group g: its lowest trial, or its middle one."""
+    return int(_load().orc_subband_nominal(g, ndm, ndm_per_nom, 1 if centred else 0))
+
+
+def subband_max_delay(delays, chans_per_sb, ndm_per_nom, centred=False) -> int:
     delays = np.ascontiguousarray(delays, dtype=np.int32)
     ndm, nchans = delays.shape
     return int(_load().orc_subband_max_delay(_ptr(delays), ndm, nchans, chans_per_sb,
-                                             ndm_per_nom))
+                                             ndm_per_nom, 1 if centred else 0))
 
 
 def subband_stage1(packed, nbits, nchans, chans_per_sb, ndm_per_nom, delays, nsamps,
-                   mask=None):
+                   mask=None, centred=False):
     """Stage 1 of Sec. 4.1; returns (S uint32 [ngroups][nsb][len1], len1)."""
     packed = np.ascontiguousarray(packed, dtype=np.uint8)
     delays = np.ascontiguousarray(delays, dtype=np.int32)
@@ -235,14 +242,14 @@ def subband_stage1(packed, nbits, nchans, chans_per_sb, ndm_per_nom, delays, nsa
     nsb = nchans // chans_per_sb
     ngroups = (ndm + ndm_per_nom - 1) // ndm_per_nom
     len1 = subband_len1(delays, chans_per_sb, nsamps)
-    need = nsamps + subband_max_delay(delays, chans_per_sb, ndm_per_nom)
+    need = nsamps + subband_max_delay(delays, chans_per_sb, ndm_per_nom, centred)
     if packed.shape[0] < need:
         raise ValueError("input holds %d rows, sub-band needs %d" % (packed.shape[0], need))
     S = np.empty((ngroups, nsb, len1), dtype=np.uint32)
     m = _mask_arr(mask, nchans)
     rc = _load().orc_subband_stage1(_ptr(packed), nbits, packed.shape[1], nchans,
-                                    chans_per_sb, ndm_per_nom, _ptr(delays), ndm,
-                                    _ptr(m), nsamps, len1, _ptr(S))
+                                    chans_per_sb, ndm_per_nom, 1 if centred else 0,
+                                    _ptr(delays), ndm, _ptr(m), nsamps, len1, _ptr(S))
     if rc != 0:
         raise ValueError("orc_subband_stage1 failed (%d)" % rc)
     return S, len1
@@ -262,9 +269,10 @@ def subband_stage2(S, nchans, chans_per_sb, ndm_per_nom, delays, nsamps) -> np.n
     return out
 
 
-def subband(packed, nbits, nchans, chans_per_sb, ndm_per_nom, delays, nsamps, mask=None):
+def subband(packed, nbits, nchans, chans_per_sb, ndm_per_nom, delays, nsamps, mask=None,
+            centred=False):
     S, _ = subband_stage1(packed, nbits, nchans, chans_per_sb, ndm_per_nom, delays,
-                          nsamps, mask)
+                          nsamps, mask, centred)
     return subband_stage2(S, nchans, chans_per_sb, ndm_per_nom, delays, nsamps)
 
 

@@ -273,14 +273,26 @@ int64_t orc_subband_len1(const int32_t *delays, int ndm, int nchans,
     return nsamps + m;
 }
 
+/* Nominal trial of group g (trials g*N'_DM .. g*N'_DM + size - 1).  The
+ * default is the group's lowest trial, the early-edge alignment App. B
+ * analyses; `centred` takes the middle trial instead, which halves the
+ * largest DM error between a trial and its nominal DM (App. B, the closing
+ * remark on aligning the sub-bands at the centre). */
+int orc_subband_nominal(int g, int ndm, int ndm_per_nom, int centred)
+{
+    int first = g * ndm_per_nom;
+    int size = ndm - first < ndm_per_nom ? ndm - first : ndm_per_nom;
+    return centred ? first + (size - 1) / 2 : first;
+}
+
 /* Input rows needed beyond nsamps: max over d, c of
  * delay(gn(d), c) - delay(gn(d), n0(c)) + delay(d, n0(c)). */
 int32_t orc_subband_max_delay(const int32_t *delays, int ndm, int nchans,
-                              int chans_per_sb, int ndm_per_nom)
+                              int chans_per_sb, int ndm_per_nom, int centred)
 {
     int32_t m = 0;
     for (int d = 0; d < ndm; ++d) {
-        int gn = (d / ndm_per_nom) * ndm_per_nom;
+        int gn = orc_subband_nominal(d / ndm_per_nom, ndm, ndm_per_nom, centred);
         const int32_t *dn = delays + (int64_t)gn * nchans;
         const int32_t *dd = delays + (int64_t)d * nchans;
         for (int c = 0; c < nchans; ++c) {
@@ -296,9 +308,9 @@ int32_t orc_subband_max_delay(const int32_t *delays, int ndm, int nchans,
  * t < nsamps + max_{d in g} delay(d, nN') (the part stage 2 reads) and is
  * zero beyond. */
 int orc_subband_stage1(const uint8_t *in, int nbits, int64_t row_stride, int nchans,
-                       int chans_per_sb, int ndm_per_nom, const int32_t *delays,
-                       int ndm, const uint8_t *mask, int64_t nsamps, int64_t len1,
-                       uint32_t *S)
+                       int chans_per_sb, int ndm_per_nom, int centred,
+                       const int32_t *delays, int ndm, const uint8_t *mask,
+                       int64_t nsamps, int64_t len1, uint32_t *S)
 {
     if (!orc_nbits_ok(nbits) || chans_per_sb <= 0 || nchans % chans_per_sb != 0 ||
         ndm_per_nom <= 0 || ndm <= 0)
@@ -309,12 +321,13 @@ int orc_subband_stage1(const uint8_t *in, int nbits, int64_t row_stride, int nch
 #pragma omp parallel for collapse(2) schedule(dynamic, 1) reduction(| : overflow)
     for (int g = 0; g < ngroups; ++g) {
         for (int n = 0; n < nsb; ++n) {
-            int gn = g * ndm_per_nom;
-            int dend = gn + ndm_per_nom < ndm ? gn + ndm_per_nom : ndm;
+            int first = g * ndm_per_nom;
+            int dend = first + ndm_per_nom < ndm ? first + ndm_per_nom : ndm;
+            int gn = orc_subband_nominal(g, ndm, ndm_per_nom, centred);
             const int32_t *dn = delays + (int64_t)gn * nchans;
             int n0 = n * chans_per_sb;
             int32_t need = 0;
-            for (int d = gn; d < dend; ++d) {
+            for (int d = first; d < dend; ++d) {
                 int32_t v = delays[(int64_t)d * nchans + n0];
                 if (v > need) need = v;
             }

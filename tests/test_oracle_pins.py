@@ -298,3 +298,60 @@ def test_subband_smear_bound_matches_taylor_form(orc):
         assert abs(ex - ty) / ex < 10 * r
     assert orc.relative_smearing(1.0, 0.0) == 1.0
     assert abs(orc.relative_smearing(3.0, 4.0) - 5.0 / 3.0) < 1e-15
+
+
+# Centred nominal DMs (App. B): the group's middle trial instead of its lowest.
+
+def test_subband_centred_nominal_index(orc):
+    # 22 trials in groups of 5: middles 2, 7, 12, 17; the short last group
+    # (trials 20, 21) keeps its lower trial
+    assert [orc.subband_nominal(g, 22, 5, True) for g in range(5)] == [2, 7, 12, 17, 20]
+    assert [orc.subband_nominal(g, 22, 5, False) for g in range(5)] == [0, 5, 10, 15, 20]
+    assert orc.subband_nominal(0, 4, 4, True) == 1
+
+
+def test_subband_centred_single_subband_is_direct_at_the_middle_trial(orc):
+    delays, packed, _ = _sb_case(orc)
+    direct = orc.direct(packed, 2, 64, 600, delays)
+    got = orc.subband(packed, 2, 64, 64, 4, delays, 600, centred=True)
+    for d in range(delays.shape[0]):
+        assert np.array_equal(got[d], direct[(d // 4) * 4 + 1])
+
+
+def test_subband_centred_nominal_trials_are_exact(orc):
+    delays, packed, _ = _sb_case(orc)
+    direct = orc.direct(packed, 2, 64, 600, delays)
+    got = orc.subband(packed, 2, 64, 16, 5, delays, 600, centred=True)
+    for g in range(4):
+        assert np.array_equal(got[g * 5 + 2], direct[g * 5 + 2])
+    one = orc.subband(packed, 2, 64, 16, 1, delays, 600, centred=True)
+    assert np.array_equal(one, direct)
+
+
+@pytest.mark.parametrize("ndn", [8, 9])
+def test_subband_centred_shrinks_the_largest_delay_error(orc, ndn):
+    # The shift a trial gets, rel(gn, c) + delay(d, n0), against its own
+    # delay(d, c) is about (DM_gn - DM_d) (dT(c) - dT(n0)).  On evenly spaced
+    # trials the early edge is N'-1 steps from the group's last trial, the
+    # middle trial ceil((N'-1)/2) steps from the farthest one: half for odd
+    # N', 4/7 for N' = 8 (up to the rounding of the differences).
+    ndm = 72
+    dms = np.linspace(0.0, 800.0, ndm)
+    delays = orc.delay_table(256, 1500.0, -0.5, 64e-6, dms).astype(np.int64)
+    nsub = 32
+
+    def worst(centred):
+        e = 0
+        for d in range(ndm):
+            gn = orc.subband_nominal(d // ndn, ndm, ndn, centred)
+            for c in range(256):
+                n0 = (c // nsub) * nsub
+                shift = delays[gn, c] - delays[gn, n0] + delays[d, n0]
+                e = max(e, abs(int(shift - delays[d, c])))
+        return e
+
+    early, mid = worst(False), worst(True)
+    ratio = ((ndn - 1) - (ndn - 1) // 2) / (ndn - 1)
+    assert early >= 20
+    assert abs(mid - early * ratio) <= 2
+    assert orc.subband_max_delay(delays.astype(np.int32), nsub, ndn, True) <= int(delays.max()) + 1
