@@ -128,6 +128,13 @@ dd_status dd_plan_set_gulp(dd_plan plan, int64_t gulp_samples);
 dd_status dd_plan_set_subband(dd_plan plan, int chans_per_subband,
                               int dms_per_nominal);
 
+/* Nominal DM of each group of N'_DM trials in the sub-band method: 0 (the
+ * default) takes the group's lowest trial, the early-edge alignment App. B
+ * analyses; 1 takes its middle trial, which halves the largest DM error
+ * between a trial and its nominal DM (App. B) and with it the smearing.
+ * Nominal trials stay exact either way. */
+dd_status dd_plan_set_subband_alignment(dd_plan plan, int centred);
+
 /* Kernel tiling: trials per thread block (16, 32 or 64), channels staged
  * per pass (4, 8, 16 or 32) and output words per lane (2, 4 or 8; compiled
  * shapes: 32x4, 64x2, 16x4, 32x2, 32x8 trials x words).  0 keeps the current

@@ -50,6 +50,7 @@ def _load_lib():
         "dd_plan_set_killmask": (I, [P, P]),
         "dd_plan_set_gulp": (I, [P, I64]),
         "dd_plan_set_subband": (I, [P, I, I]),
+        "dd_plan_set_subband_alignment": (I, [P, I]),
         "dd_plan_set_tuning": (I, [P, I, I, I]),
         "dd_plan_get_tuning": (I, [P, pp(I), pp(I), pp(I)]),
         "dd_plan_autotune": (I, [P, I, I64, P]),
@@ -203,9 +204,17 @@ class Plan:
             raise ValueError("kill mask needs one entry per channel")
         _check(_lib.dd_plan_set_killmask(self._h, m.ctypes.data), "dd_plan_set_killmask")
 
-    def set_subband(self, chans_per_subband, dms_per_nominal):
+    def set_subband(self, chans_per_subband, dms_per_nominal, centred=None):
         _check(_lib.dd_plan_set_subband(self._h, int(chans_per_subband), int(dms_per_nominal)),
                "dd_plan_set_subband")
+        if centred is not None:
+            self.set_subband_alignment(centred)
+
+    def set_subband_alignment(self, centred):
+        """Nominal DM of each trial group: its middle trial (True) or its
+        lowest (False, the default)."""
+        _check(_lib.dd_plan_set_subband_alignment(self._h, 1 if centred else 0),
+               "dd_plan_set_subband_alignment")
 
     def set_tuning(self, dms_per_block=0, chans_per_chunk=0, words_per_lane=0):
         _check(_lib.dd_plan_set_tuning(self._h, int(dms_per_block), int(chans_per_chunk),

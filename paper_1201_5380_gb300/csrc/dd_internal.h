@@ -185,6 +185,7 @@ struct Plan {
   int32_t max_delay = 0;
   int64_t gulp = 0;
   int sb_chans = 0, sb_dms = 0;  // sub-band N', N'_DM (0 = off)
+  bool sb_centred = false;       // nominal trial: group's middle (else lowest)
   Tuning tune;
   bool tuned_by_search = false;
   int num_sms = 0;

@@ -161,7 +161,8 @@ dd_status ensure_device_tables(Plan& p) {
 
 // Sub-band tables (Sec. 4.1).  Trials are grouped N'_DM at a time; group g's
 // nominal trial is g*N'_DM (its lowest DM, the early-edge alignment of
-// App. B).  Stage-1 shifts are differences of rounded delays,
+// App. B) or, centred, the group's middle trial (half the DM error, App. B).
+// Stage-1 shifts are differences of rounded delays,
 //   rel[g][c] = delay(gn, c) - delay(gn, n0(c)),
 // and stage-2 shifts are delay(d, nN'), the telescoped sum of
 // Eq. (eq:combining_subbands).
@@ -174,7 +175,9 @@ dd_status prepare_subband(Plan& p) {
   p.sb_d2.assign((size_t)n * nsb, 0);
   int32_t mx = 0, m2 = 0;
   for (int g = 0; g < ng; ++g) {
-    const int32_t* dn = &p.delays[(size_t)g * p.sb_dms * C];
+    const int first = g * p.sb_dms, size = std::min(p.sb_dms, n - first);
+    const int gn = p.sb_centred ? first + (size - 1) / 2 : first;
+    const int32_t* dn = &p.delays[(size_t)gn * C];
     for (int c = 0; c < C; ++c) {
       const int n0 = (c / Np) * Np;
       p.sb_rel[(size_t)g * C + c] = dn[c] - dn[n0];
@@ -418,6 +421,16 @@ dd_status dd_plan_set_gulp(dd_plan plan, int64_t gulp) {
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (!p || gulp <= 0) return DD_ERR_INVALID_ARG;
   p->gulp = gulp;
+  return DD_OK;
+}
+
+dd_status dd_plan_set_subband_alignment(dd_plan plan, int centred) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p || (centred != 0 && centred != 1)) return DD_ERR_INVALID_ARG;
+  if (p->sb_centred != (centred == 1)) {
+    p->sb_centred = centred == 1;
+    p->sb_dirty = true;
+  }
   return DD_OK;
 }
 

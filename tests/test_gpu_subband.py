@@ -11,11 +11,11 @@ from _gpu import odelays, run_direct, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-def _plan(step=1, nsub=32, ndmn=32):
+def _plan(step=1, nsub=32, ndmn=32, centred=False):
     c = configs.SUBBAND
     full = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
     return dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dms=full.dms[::step],
-                   subband=(nsub, ndmn))
+                   subband=(nsub, ndmn, centred))
 
 
 def test_subband_survey_band_bit_exact(orc):
@@ -26,6 +26,23 @@ def test_subband_survey_band_bit_exact(orc):
     got, _ = run_direct(plan, x, 2, nsamps, subband=True)
     ref = orc.subband(x, 2, 1024, 32, 32, odelays(orc, plan), nsamps)
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("centred", [False, True])
+def test_subband_centred_alignment_bit_exact(orc, centred):
+    # 100 trials in groups of 32 (short last group), survey band
+    plan = _plan(step=12, centred=centred)
+    nsamps = 1700
+    rows = nsamps + plan.subband_max_delay
+    x = synth.uniform_packed(24, 0, rows, 1024, 2)
+    got, _ = run_direct(plan, x, 2, nsamps, subband=True)
+    ref = orc.subband(x, 2, 1024, 32, 32, odelays(orc, plan), nsamps, centred=centred)
+    assert np.array_equal(got, ref)
+    # the nominal trials are exact direct sums
+    di, _ = run_direct(plan, x, 2, nsamps)
+    for g in range((plan.dm_count + 31) // 32):
+        gn = orc.subband_nominal(g, plan.dm_count, 32, centred)
+        assert np.array_equal(got[gn], di[gn])
 
 
 @pytest.mark.parametrize("nsub,ndmn,nbits", [(16, 8, 2), (64, 16, 4), (32, 5, 8), (8, 32, 1)])

@@ -72,12 +72,13 @@ def test_user_dm_list_delays_match_oracle(orc):
                           orc.delay_table(c["nchans"], c["f0"], c["df"], c["dt"], dms))
 
 
+@pytest.mark.parametrize("centred", [False, True])
 @pytest.mark.parametrize("nsub,ndmn", [(32, 32), (16, 8), (1, 4), (8, 1)])
-def test_subband_max_delay_matches_oracle(orc, nsub, ndmn):
+def test_subband_max_delay_matches_oracle(orc, nsub, ndmn, centred):
     c = configs.SURVEY
     p = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0),
-                subband=(nsub, ndmn))
-    assert p.subband_max_delay == orc.subband_max_delay(p.delay_table(), nsub, ndmn)
+                subband=(nsub, ndmn, centred))
+    assert p.subband_max_delay == orc.subband_max_delay(p.delay_table(), nsub, ndmn, centred)
 
 
 def test_plan_validation():
