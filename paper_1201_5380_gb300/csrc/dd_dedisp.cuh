@@ -57,6 +57,16 @@ template <bool WIDE> struct Acc<FMT_NIB, WIDE> {
     b1 += (n >> 4) & 0x0F0F0F0Fu;
     n = 0u;
   }
+  // Two groups of four channels whose 4-bit sums each fit a nibble (f0 ==
+  // 1), widened to the 8-bit lanes together: one add per lane set for both.
+  __device__ __forceinline__ void add8_flush(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
+                                             uint32_t x4, uint32_t x5, uint32_t x6,
+                                             uint32_t x7) {
+    const uint32_t a = (x0 + x1) + (x2 + x3);
+    const uint32_t c = (x4 + x5) + (x6 + x7);
+    b0 += (a & 0x0F0F0F0Fu) + (c & 0x0F0F0F0Fu);
+    b1 += ((a >> 4) & 0x0F0F0F0Fu) + ((c >> 4) & 0x0F0F0F0Fu);
+  }
   __device__ __forceinline__ void flush1() {
     h0 += b0 & 0x00FF00FFu;
     h1 += (b0 >> 8) & 0x00FF00FFu;
@@ -486,6 +496,46 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       const uint32_t lane_off =
           (COPIES ? smem_addr(copies + buf * copy_words) : smem_addr(landing + buf * landing_words)) +
           (uint32_t)lane * 4u;
+      bool paired = false;
+      if constexpr (FMT == FMT_NIB) paired = p.f0 == 1 && p.f1 >= 2 && (cc & 7) == 0;
+      if (paired) {
+        // 2-bit input: pairs of 4-channel groups widened together; a pair
+        // adds at most two group sums to a byte lane, so the 16-bit flush
+        // comes every f1/2 pairs
+        if constexpr (FMT == FMT_NIB)
+        for (int cg = 0; cg < cc; cg += 8) {
+#pragma unroll
+          for (int i = 0; i < DPW; ++i) {
+            const uint32_t* const e = sa + ((warp * DPW + i) << cc_log) + cg;
+            const uint4 a4 = *reinterpret_cast<const uint4*>(e);
+            const uint4 b4 = *reinterpret_cast<const uint4*>(e + 4);
+            const uint32_t q0 = a4.x + lane_off, q1 = a4.y + lane_off;
+            const uint32_t q2 = a4.z + lane_off, q3 = a4.w + lane_off;
+            const uint32_t q4 = b4.x + lane_off, q5 = b4.y + lane_off;
+            const uint32_t q6 = b4.z + lane_off, q7 = b4.w + lane_off;
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+              acc[i][j].add8_flush(lds32(q0 + 128u * j), lds32(q1 + 128u * j),
+                                   lds32(q2 + 128u * j), lds32(q3 + 128u * j),
+                                   lds32(q4 + 128u * j), lds32(q5 + 128u * j),
+                                   lds32(q6 + 128u * j), lds32(q7 + 128u * j));
+          }
+          if (++g1 == (p.f1 >> 1)) {
+            g1 = 0;
+#pragma unroll
+            for (int i = 0; i < DPW; ++i)
+#pragma unroll
+              for (int j = 0; j < K; ++j) acc[i][j].flush1();
+            if (WIDE && ++g2 == p.f2) {
+              g2 = 0;
+#pragma unroll
+              for (int i = 0; i < DPW; ++i)
+#pragma unroll
+                for (int j = 0; j < K; ++j) acc[i][j].flush2();
+            }
+          }
+        }
+      } else
       for (int cg = 0; cg < cc; cg += 4) {
 #pragma unroll
         for (int i = 0; i < DPW; ++i) {
