@@ -126,7 +126,7 @@ class ClockSampler:
 
 # DRAM bytes (read + write) of one dedispersion launch on the survey band at
 # 2^17 output samples, from ncu; the traffic grows in proportion to the gulp.
-DEDISP_TRAFFIC_2E17 = 78.999040e6 + 568.750336e6
+DEDISP_TRAFFIC_2E17 = 77.903616e6 + 569.380864e6
 
 
 def cpu_oracle_rate(x, delays, G, seconds):
