@@ -269,6 +269,29 @@ dd_status dd_batch_add(dd_batch batch, dd_stream stream, const void *in_dev,
  * (asynchronous); nsamps_out[i] receives the outputs of the i-th add. */
 dd_status dd_batch_launch(dd_batch batch, void *cuda_stream, int64_t *nsamps_out);
 
+/* ---- graph: a batch's launch captured once, replayed gulp after gulp
+ *
+ * In steady-state streaming every gulp of a batch does the same GPU work
+ * (appends, corner turns, one persistent launch, tail moves) on the same
+ * buffers, apart from each stream's two tail buffers, which swap roles every
+ * push.  dd_batch_graph_create records the batch's current adds as two CUDA
+ * graphs (one per tail-buffer role) and dd_batch_graph_launch replays the
+ * one that matches, then advances the streams as dd_batch_launch would, so
+ * a gulp costs one graph launch instead of dozens of calls.
+ * Requirements: every stream of the batch is primed (its overlap tail is
+ * full: it has taken at least max_delay input rows), the same adds (the
+ * same device buffers and gulp sizes) were launched once with
+ * dd_batch_launch, which sizes the buffers the capture reuses, and neither
+ * the batch, its streams, their plans nor the buffers change while the
+ * graph is used; the caller refills the input buffers between replays.
+ * Returns DD_ERR_INVALID_ARG when a stream is not primed. */
+typedef struct dd_batch_graph_s *dd_batch_graph;
+dd_status dd_batch_graph_create(dd_batch_graph *graph, dd_batch batch);
+/* Replay on cuda_stream (asynchronous); nsamps_out[i] receives the outputs
+ * of the i-th add. */
+dd_status dd_batch_graph_launch(dd_batch_graph graph, void *cuda_stream, int64_t *nsamps_out);
+void dd_batch_graph_destroy(dd_batch_graph graph);
+
 /* ---- serving: gulps of many beams as they arrive (continuous batching)
  *
  * The paper processes fixed blocks one at a time and has no serving layer;

@@ -77,6 +77,9 @@ def _load_lib():
         "dd_batch_clear": (I, [P]),
         "dd_batch_add": (I, [P, P, P, I64, I64, P, I64]),
         "dd_batch_launch": (I, [P, P, P]),
+        "dd_batch_graph_create": (I, [pp(P), P]),
+        "dd_batch_graph_launch": (I, [P, P, P]),
+        "dd_batch_graph_destroy": (None, [P]),
         "dd_probe_int_add": (I, [I64, P, pp(D), pp(D)]),
         "dd_server_create": (I, [pp(P), ctypes.c_size_t, I, I]),
         "dd_server_destroy": (None, [P]),
@@ -406,6 +409,10 @@ class Batch:
                "dd_batch_launch")
         return n[:self._n]
 
+    def capture(self):
+        """CUDA graphs of this batch's adds for steady-state replay."""
+        return BatchGraph(self)
+
 
 class RequestInfo(ctypes.Structure):
     """A completed serving request (dd_request_info)."""
@@ -498,6 +505,35 @@ class Server:
         _check(_lib.dd_server_stats(self._h, ctypes.byref(q), ctypes.byref(f), ctypes.byref(c),
                                     ctypes.byref(u)), "dd_server_stats")
         return dict(queued=q.value, inflight=f.value, completed=c.value, arena_used=u.value)
+
+
+class BatchGraph:
+    """A batch's launch captured as CUDA graphs (steady-state streaming):
+    ``launch`` replays it on the same buffers, one gulp per call."""
+
+    def __init__(self, batch):
+        h = ctypes.c_void_p()
+        _check(_lib.dd_batch_graph_create(ctypes.byref(h), batch._h), "dd_batch_graph_create")
+        self._h = h
+        self._batch = batch  # the graph replays the batch's adds
+        self._n = batch._n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dd_batch_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch(self, stream=None):
+        n = np.zeros(max(1, self._n), dtype=np.int64)
+        _check(_lib.dd_batch_graph_launch(self._h, _stream_ptr(stream), n.ctypes.data),
+               "dd_batch_graph_launch")
+        return n[:self._n]
 
 
 def probe_int_add(adds_per_thread=1 << 16, stream=None):

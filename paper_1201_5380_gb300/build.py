@@ -63,6 +63,14 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     jobs = min(len(srcs), max(1, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
+    # objects of earlier header versions are never linked again
+    keep = {os.path.basename(o) for o in objs}
+    for f in os.listdir(OBJDIR):
+        if f.endswith(".o") and f not in keep:
+            try:
+                os.remove(os.path.join(OBJDIR, f))
+            except OSError:
+                pass
     newest = max(os.path.getmtime(o) for o in objs)
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= newest and not ptxas_info:
         return LIB

@@ -9,6 +9,7 @@
 // overlap that makes consecutive blocks equal one continuous transform.
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <new>
 
 #include "dd_internal.h"
@@ -332,6 +333,98 @@ dd_status dd_batch_launch(dd_batch b, void* cuda_stream, int64_t* nsamps_out) {
   }
   return DD_OK;
 }
+
+// Graph capture of a batch launch (steady-state streaming).  The capture
+// runs dd_batch_launch's host logic on a capturing stream, so every copy,
+// memset and kernel it issues becomes a graph node; the streams' host state
+// that the capture advanced is then put back, and each replay advances it.
+struct dd_batch_graph_s {
+  dd_batch batch = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  int cur0 = 0;                   // first stream's tail buffer when variant 0 was taken
+  std::vector<int64_t> nouts;     // outputs per add (the same on every replay)
+  ~dd_batch_graph_s() {
+    for (auto& e : exec)
+      if (e) cudaGraphExecDestroy(e);
+  }
+};
+
+dd_status dd_batch_graph_create(dd_batch_graph* out, dd_batch b) {
+  if (!out || !b || b->items.empty()) return DD_ERR_INVALID_ARG;
+  *out = nullptr;
+  const size_t n = b->items.size();
+  for (const BatchItem& it : b->items) {
+    const StreamState& s = it.stream->s;
+    if (s.tail_rows != s.plan->max_delay || it.n_in <= 0) return DD_ERR_INVALID_ARG;
+  }
+  std::unique_ptr<dd_batch_graph_s> g(new (std::nothrow) dd_batch_graph_s());
+  if (!g) return DD_ERR_OOM;
+  g->batch = b;
+  g->nouts.assign(n, 0);
+  g->cur0 = b->items[0].stream->s.cur;
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_status(e);
+  dd_status result = DD_OK;
+  for (int v = 0; v < 2 && result == DD_OK; ++v) {
+    // save what the capture advances; take variant 1 with the tail buffers swapped
+    std::vector<StreamState*> ss;
+    std::vector<int> cur;
+    std::vector<int64_t> tail, sin, sout;
+    std::vector<bool> timing;
+    for (BatchItem& it : b->items) {
+      StreamState& s = it.stream->s;
+      ss.push_back(&s);
+      cur.push_back(s.cur);
+      tail.push_back(s.tail_rows);
+      sin.push_back(s.samples_in);
+      sout.push_back(s.samples_out);
+      timing.push_back(s.plan->timing);
+      s.plan->timing = false;  // no timing events inside a graph
+      if (v == 1) s.cur ^= 1;
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      result = dd_batch_launch(b, cs, g->nouts.data());
+      e = cudaStreamEndCapture(cs, &graph);
+      if (e == cudaSuccess && result == DD_OK)
+        e = cudaGraphInstantiate(&g->exec[v], graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+    }
+    if (e != cudaSuccess && result == DD_OK) result = cuda_status(e);
+    for (size_t i = 0; i < ss.size(); ++i) {
+      ss[i]->cur = cur[i];
+      ss[i]->tail_rows = tail[i];
+      ss[i]->samples_in = sin[i];
+      ss[i]->samples_out = sout[i];
+      ss[i]->plan->timing = timing[i];
+    }
+  }
+  cudaStreamDestroy(cs);
+  cudaGetLastError();
+  if (result != DD_OK) return result;
+  *out = g.release();
+  return DD_OK;
+}
+
+dd_status dd_batch_graph_launch(dd_batch_graph g, void* cuda_stream, int64_t* nsamps_out) {
+  if (!g || !nsamps_out) return DD_ERR_INVALID_ARG;
+  dd_batch b = g->batch;
+  const int v = b->items[0].stream->s.cur == g->cur0 ? 0 : 1;
+  cudaError_t e = cudaGraphLaunch(g->exec[v], static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_status(e);
+  for (size_t i = 0; i < b->items.size(); ++i) {
+    StreamState& s = b->items[i].stream->s;
+    s.samples_in += b->items[i].n_in;
+    s.samples_out += g->nouts[i];
+    s.cur ^= 1;  // the tail moved to the other buffer
+    nsamps_out[i] = g->nouts[i];
+  }
+  return DD_OK;
+}
+
+void dd_batch_graph_destroy(dd_batch_graph g) { delete g; }
 
 // Autotuner: time each compiled tile shape x chunk size on nsamps synthetic
 // samples (zeros: the kernel's cost does not depend on the values) and keep

@@ -121,3 +121,57 @@ def test_batch_equals_individual_streams(orc):
         assert np.array_equal(gb, gs)
         nout = sum(gulps[i]) - p.max_delay
         assert np.array_equal(gb, orc.direct(xs[i], 8, p.nchans, nout, odelays(orc, p)))
+
+
+def test_batch_graph_replay_equals_the_oracle(orc):
+    """A captured batch launch replayed gulp after gulp (new data written
+    into the same input buffers) continues every beam's series exactly."""
+    torch = torch_cuda()
+    plans = [_plan(256, 40, 400.0), _plan(128, 23, 300.0), _plan(256, 17, 250.0)]
+    G = 2048
+    ngulps = 6
+    xs = [synth.uniform_packed(90 + i, 2, G * ngulps, p.nchans, 2) for i, p in enumerate(plans)]
+    ins = [torch.zeros((G, p.nchans // 4), dtype=torch.uint8, device="cuda") for p in plans]
+    outs = [torch.zeros((p.dm_count, G), dtype=torch.int32, device="cuda") for p in plans]
+    streams = [dd.Stream(p, 2, G) for p in plans]
+    batch = dd.Batch()
+    for i in range(3):
+        batch.add(streams[i], ins[i], G, outs[i])
+    got = [[] for _ in plans]
+
+    def load(k):
+        for i in range(3):
+            ins[i].copy_(torch.from_numpy(np.ascontiguousarray(xs[i][k * G:(k + 1) * G])))
+
+    def collect(nouts):
+        torch.cuda.synchronize()
+        for i in range(3):
+            got[i].append(outs[i][:, :nouts[i]].cpu().numpy().view(np.uint32).copy())
+
+    for k in range(2):                 # prime the tails and warm the buffers
+        load(k)
+        collect(batch.launch())
+    graph = batch.capture()
+    for k in range(2, ngulps):
+        load(k)
+        collect(graph.launch())
+    for i, p in enumerate(plans):
+        series = np.concatenate(got[i], axis=1)
+        nout = G * ngulps - p.max_delay
+        assert series.shape[1] == nout
+        assert streams[i].position() == (G * ngulps, nout)
+        ref = orc.direct(xs[i], 2, p.nchans, nout, odelays(orc, p))
+        assert np.array_equal(series, ref), i
+
+
+def test_batch_graph_needs_primed_streams():
+    torch_cuda()
+    import torch
+    p = _plan(128, 10, 300.0)
+    s = dd.Stream(p, 2, 1000)
+    b = dd.Batch()
+    x = torch.zeros((1000, 32), dtype=torch.uint8, device="cuda")
+    o = torch.zeros((p.dm_count, 1000), dtype=torch.int32, device="cuda")
+    b.add(s, x, 1000, o)
+    with pytest.raises(dd.DedispError):
+        b.capture()                    # tail still empty
