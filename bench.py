@@ -454,6 +454,59 @@ def run_subband(a, x, plan_direct, d_out_direct, G):
     return res
 
 
+def run_graph(a):
+    """Steady-state streaming of the 13 serving beams at 2^14 samples per
+    gulp (device buffers): per gulp, host time to submit the work (median,
+    nothing queued ahead) and GPU time (back to back), for dd_batch_launch
+    against a replay of its captured CUDA graphs."""
+    import torch
+    import paper_1201_5380_gb300 as dd
+
+    c = configs.SERVING
+    G = 1 << 14
+    plans = []
+    for b in range(c["nbeams"]):
+        band = c["bands"][b % 2]
+        plans.append(dd.Plan(band["nchans"], c["dt"], band["f0"], band["df"],
+                             dm_rule=dict(lo=c["dms"]["lo"], hi=c["dms"]["hi"])))
+    st = torch.cuda.Stream()
+    res = {"workload": "13 serving beams, 8-bit, 2^14 samples per gulp, device buffers"}
+    for mode in ("batch", "graph"):
+        streams = [dd.Stream(p, 8, G) for p in plans]
+        ins = [torch.from_numpy(synth.uniform_packed(7, b, G, p.nchans, 8)).cuda()
+               for b, p in enumerate(plans)]
+        outs = [torch.empty((p.dm_count, G), dtype=torch.int32, device="cuda") for p in plans]
+        batch = dd.Batch()
+        for i in range(len(plans)):
+            batch.add(streams[i], ins[i], G, outs[i])
+        prime = max(-(-p.max_delay // G) for p in plans) + 1
+        for _ in range(prime):
+            batch.launch(stream=st)
+        launch = batch.capture().launch if mode == "graph" else batch.launch
+        for _ in range(3):
+            launch(stream=st)
+        st.synchronize()
+        reps = 30
+        # host cost of submitting one gulp, with nothing queued ahead of it
+        host = []
+        for _ in range(10):
+            st.synchronize()
+            t0 = time.perf_counter()
+            launch(stream=st)
+            host.append(time.perf_counter() - t0)
+        st.synchronize()
+        # GPU time per gulp, back to back
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(st)
+        for _ in range(reps):
+            launch(stream=st)
+        ev[1].record(st)
+        st.synchronize()
+        res[mode] = {"host_submit_us_per_gulp": float(np.median(host)) * 1e6,
+                     "gpu_ms_per_gulp": ev[0].elapsed_time(ev[1]) / reps}
+    return res
+
+
 def replica_throughput(local_ms, units_per_rank, world, device):
     """Whole-job throughput of `world` replicas that each processed
     units_per_rank units in local_ms: the slowest rank's time (max over
@@ -585,6 +638,7 @@ def run_ours(a, rank, world, local_rank):
         del d_in, out
         torch.cuda.empty_cache()
         line["serving"] = run_serving(a)
+        line["serving"]["graph_replay"] = run_graph(a)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         import oracle
         oracle.build()
