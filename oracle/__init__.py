@@ -71,6 +71,8 @@ def _load():
                                                      ctypes.c_int, P, P, P, P]),
             "orc_subband_len1": (i64, [P, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, i64]),
+            "orc_diagonal_dm": (f64, [f64, f64, f64]),
+            "orc_scrunch_factor": (ctypes.c_int, [f64, f64, ctypes.c_int]),
             "orc_subband_nominal": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_int, ctypes.c_int]),
             "orc_subband_max_delay": (i32, [P, ctypes.c_int, ctypes.c_int,
@@ -213,6 +215,49 @@ def direct_points_f32(data, delays, dsel, tsel, mask=None):
     if rc != 0:
         raise ValueError("orc_direct_points_f32 failed (%d)" % rc)
     return out, ab
+
+
+def diagonal_dm(f0, df, dt) -> float:
+    """Sec. 2.2: DM at which the smallest per-channel delay step is 1 sample."""
+    return float(_load().orc_diagonal_dm(f0, df, dt))
+
+
+def scrunch_factors(dms, f0, df, dt, max_factor=16) -> np.ndarray:
+    """Per-trial time-scrunch factor: 1 below 2x the diagonal DM, then 2, 4,
+    ... doubling at each further doubling of the diagonal."""
+    diag = diagonal_dm(f0, df, dt)
+    return np.array([_load().orc_scrunch_factor(float(d), diag, int(max_factor)) for d in dms],
+                    dtype=np.int32)
+
+
+def scrunch(samples, s) -> np.ndarray:
+    """Sec. 2.2: sum s adjacent time samples (rows) of an unpacked
+    [rows][nchans] array; the last rows % s samples are dropped."""
+    samples = np.asarray(samples)
+    rows = samples.shape[0] // s * s
+    return samples[:rows].reshape(-1, s, samples.shape[1]).sum(axis=1, dtype=np.uint32)
+
+
+def direct_scrunched(samples, nchans, nsamps, f0, df, dt, dms, max_factor=16, mask=None):
+    """Direct dedispersion with time-scrunching (Sec. 2.2) from unpacked
+    samples [rows][nchans] (values < 256 // max_factor).  Trials of scrunch
+    factor s are dedispersed at resolution s*dt: the input scrunched by s,
+    delays from Eq. 3-4 with dt -> s*dt, nsamps // s outputs.  Returns
+    (uint32 [ndm][nsamps] with row d valid for nsamps // s_d samples and zero
+    after, factors)."""
+    dms = np.asarray(dms, dtype=np.float64)
+    fac = scrunch_factors(dms, f0, df, dt, max_factor)
+    out = np.zeros((dms.size, nsamps), dtype=np.uint32)
+    for s in sorted(set(fac.tolist())):
+        sel = np.nonzero(fac == s)[0]
+        delays = delay_table(nchans, f0, df, dt * s, dms[sel])
+        a = scrunch(samples, s) if s > 1 else np.asarray(samples, dtype=np.uint32)
+        if a.max(initial=0) > 255:
+            raise ValueError("scrunched samples exceed 8 bits")
+        packed = np.ascontiguousarray(a.astype(np.uint8))
+        n = nsamps // s
+        out[sel, :n] = direct(packed, 8, nchans, n, delays, mask)
+    return out, fac
 
 
 def subband_len1(delays, chans_per_sb, nsamps) -> int:

@@ -70,6 +70,29 @@ double orc_partial_delay(double f0_mhz, double df_mhz, double dt_s, int chan)
     return (ORC_K_DM / dt_s) * (1.0 / (f * f) - 1.0 / (f0_mhz * f0_mhz));
 }
 
+/* Sec. 2.2, time-scrunching.  The "diagonal" DM is where the dispersion
+ * curve's gradient on the time-frequency grid reaches one sample per channel
+ * everywhere in the band: where the smallest per-channel delay step, between
+ * the two highest channels (0 and 1), equals one sample.  This reading (the
+ * paper does not say which channel pair) reproduces the paper's projected
+ * 1.6x saving on its survey band (Sec. 5.2); see the pins. */
+double orc_diagonal_dm(double f0_mhz, double df_mhz, double dt_s)
+{
+    double step = orc_partial_delay(f0_mhz, df_mhz, dt_s, 1) -
+                  orc_partial_delay(f0_mhz, df_mhz, dt_s, 0);
+    return step > 0.0 ? 1.0 / step : 0.0;
+}
+
+/* Scrunch factor of a trial (Sec. 2.2 and the projection of Sec. 5.2):
+ * full resolution below twice the diagonal, then 2 up to 4x the diagonal,
+ * 4 up to 8x and so on (at most max_factor). */
+int orc_scrunch_factor(double dm, double diag, int max_factor)
+{
+    int s = 1;
+    while (s < max_factor && diag > 0.0 && dm >= 2.0 * (double)s * diag) s *= 2;
+    return s;
+}
+
 /* Eq. 4 for every (d, c): out[d*nchans + c] = round(DM(d) * Delta T(c)).
  * Returns 0, or -1 on a bad argument (non-positive frequency, negative
  * delay or a delay that does not fit in int32). */
