@@ -78,6 +78,8 @@ typedef enum dd_status {
                                computes, copies out and synchronises. */
 #define DD_SUBBAND 0x2u     /* use the two-stage sub-band method (needs
                                dd_plan_set_subband) instead of direct */
+#define DD_SCRUNCH 0x4u     /* direct with time-scrunching (needs
+                               dd_plan_set_scrunch; device pointers) */
 
 typedef struct dd_plan_s *dd_plan;
 typedef struct dd_stream_s *dd_stream;
@@ -134,6 +136,21 @@ dd_status dd_plan_set_subband(dd_plan plan, int chans_per_subband,
  * between a trial and its nominal DM (App. B) and with it the smearing.
  * Nominal trials stay exact either way. */
 dd_status dd_plan_set_subband_alignment(dd_plan plan, int centred);
+
+/* Time-scrunching (Sec. 2.2): trials beyond twice the diagonal DM (where
+ * the top two channels' delays differ by one sample) are dedispersed at
+ * half the time resolution, at a quarter beyond four times it, and so on up
+ * to max_factor (a power of two, at most 16; 0 turns it off).  A trial of
+ * factor s sums s adjacent input samples and uses Eq. 3-4 at s*dt; its output
+ * row holds nsamps_out / s samples (the rest of the row is not written).
+ * Input of 1, 2 or 4 bits per sample only.  Execute with DD_SCRUNCH. */
+dd_status dd_plan_set_scrunch(dd_plan plan, int max_factor);
+/* Factor of every trial (1 when scrunching is off). */
+dd_status dd_plan_get_scrunch_factors(dd_plan plan, int32_t *factors);
+/* Input rows an execute of nsamps_out samples reads with these flags
+ * (DD_SUBBAND / DD_SCRUNCH): nsamps_out + max_delay for direct. */
+dd_status dd_plan_get_input_rows(dd_plan plan, int64_t nsamps_out, unsigned flags,
+                                 int64_t *rows);
 
 /* Kernel tiling: trials per thread block (16, 32 or 64), channels staged
  * per pass (4, 8, 16 or 32) and output words per lane (2, 4 or 8; compiled

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libgb300dd.so")
 
 DD_DEVICE_PTRS = 0x1
 DD_SUBBAND = 0x2
+DD_SCRUNCH = 0x4
 DD_IN_F32 = 32
 
 STATUS = {
@@ -51,6 +52,9 @@ def _load_lib():
         "dd_plan_set_gulp": (I, [P, I64]),
         "dd_plan_set_subband": (I, [P, I, I]),
         "dd_plan_set_subband_alignment": (I, [P, I]),
+        "dd_plan_set_scrunch": (I, [P, I]),
+        "dd_plan_get_scrunch_factors": (I, [P, P]),
+        "dd_plan_get_input_rows": (I, [P, I64, ctypes.c_uint, pp(I64)]),
         "dd_plan_set_tuning": (I, [P, I, I, I]),
         "dd_plan_get_tuning": (I, [P, pp(I), pp(I), pp(I)]),
         "dd_plan_autotune": (I, [P, I, I64, P]),
@@ -213,6 +217,26 @@ class Plan:
         if centred is not None:
             self.set_subband_alignment(centred)
 
+    def set_scrunch(self, max_factor):
+        """Time-scrunching (Sec. 2.2) up to max_factor (power of two <= 16;
+        0 turns it off); execute with scrunch=True."""
+        _check(_lib.dd_plan_set_scrunch(self._h, int(max_factor)), "dd_plan_set_scrunch")
+
+    @property
+    def scrunch_factors(self):
+        out = np.zeros(self.dm_count, dtype=np.int32)
+        _check(_lib.dd_plan_get_scrunch_factors(self._h, out.ctypes.data),
+               "dd_plan_get_scrunch_factors")
+        return out
+
+    def input_rows(self, nsamps_out, subband=False, scrunch=False):
+        """Input rows an execute of nsamps_out samples reads."""
+        r = ctypes.c_int64()
+        flags = (DD_SUBBAND if subband else 0) | (DD_SCRUNCH if scrunch else 0)
+        _check(_lib.dd_plan_get_input_rows(self._h, int(nsamps_out), flags, ctypes.byref(r)),
+               "dd_plan_get_input_rows")
+        return r.value
+
     def set_subband_alignment(self, centred):
         """Nominal DM of each trial group: its middle trial (True) or its
         lowest (False, the default)."""
@@ -284,7 +308,7 @@ class Plan:
     def reset_kernel_timing(self):
         _check(_lib.dd_plan_reset_kernel_timing(self._h), "dd_plan_reset_kernel_timing")
 
-    def execute(self, inp, nbits, nsamps_out, out, stream=None, subband=False):
+    def execute(self, inp, nbits, nsamps_out, out, stream=None, subband=False, scrunch=False):
         """Dedisperse ``nsamps_out`` samples of ``inp`` (rows = time, packed
         channel bytes or float channels) into ``out`` ([ndm][>= nsamps_out],
         uint32/int32 or float32).  Both on the device (torch CUDA tensors,
@@ -296,7 +320,8 @@ class Plan:
         esize = out.element_size() if _is_torch(out) else out.itemsize
         if esize != 4:
             raise ValueError("output elements must be 32-bit")
-        flags = (DD_DEVICE_PTRS if idev else 0) | (DD_SUBBAND if subband else 0)
+        flags = ((DD_DEVICE_PTRS if idev else 0) | (DD_SUBBAND if subband else 0) |
+                 (DD_SCRUNCH if scrunch else 0))
         _check(_lib.dd_execute(self._h, int(nsamps_out), ip, int(nbits), int(istride), op,
                                int(ostride // 4), _stream_ptr(stream), flags), "dd_execute")
         return out

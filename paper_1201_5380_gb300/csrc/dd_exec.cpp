@@ -691,13 +691,22 @@ extern "C" dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void* in
       in_nbits == 32 ? (int64_t)p->nchans * 4 : ((int64_t)p->nchans * in_nbits + 7) / 8;
   if (in_row_stride < row_bytes) return DD_ERR_INVALID_ARG;
   const bool sub = (flags & DD_SUBBAND) != 0;
+  const bool scr = (flags & DD_SCRUNCH) != 0;
   if (sub && p->sb_chans <= 0) return DD_ERR_INVALID_ARG;
+  if (scr && (sub || p->scrunch_max <= 0 || !(flags & DD_DEVICE_PTRS)))
+    return DD_ERR_INVALID_ARG;
+  if (scr && in_nbits > 4) return DD_ERR_UNSUPPORTED_NBITS;
   std::lock_guard<std::mutex> lk(p->mu);
   if (sub) {
     dd_status s = prepare_subband(*p);
     if (s != DD_OK) return s;
   }
-  const int64_t rows = nsamps_out + (sub ? p->sb_max_delay : p->max_delay);
+  if (scr) {
+    dd_status s = prepare_scrunch(*p);
+    if (s != DD_OK) return s;
+  }
+  const int64_t rows = scr ? scrunch_input_rows(*p, nsamps_out)
+                           : nsamps_out + (sub ? p->sb_max_delay : p->max_delay);
   ExecArgs a;
   a.nsamps_out = nsamps_out;
   a.in_nbits = in_nbits;
@@ -713,7 +722,7 @@ extern "C" dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void* in
     if (!device_range_ok(out, out_bytes)) return DD_ERR_INVALID_ARG;
     a.in = in;
     a.out = out;
-    return exec_device(*p, a);
+    return scr ? exec_scrunch(*p, a) : exec_device(*p, a);
   }
   // host pointers: stage through plan-owned device buffers
   cudaError_t e;
@@ -731,6 +740,28 @@ extern "C" dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void* in
                              a.st)) != cudaSuccess)
     return cuda_status(e);
   if ((e = cudaStreamSynchronize(a.st)) != cudaSuccess) return cuda_status(e);
+  return DD_OK;
+}
+
+extern "C" dd_status dd_plan_get_input_rows(dd_plan plan, int64_t nsamps_out, unsigned flags,
+                                           int64_t* rows) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p || !rows || nsamps_out < 0) return DD_ERR_INVALID_ARG;
+  if (p->dms.empty()) return DD_ERR_NO_DM_LIST;
+  std::lock_guard<std::mutex> lk(p->mu);
+  if (flags & DD_SCRUNCH) {
+    if (p->scrunch_max <= 0) return DD_ERR_INVALID_ARG;
+    dd_status s = prepare_scrunch(*p);
+    if (s != DD_OK) return s;
+    *rows = scrunch_input_rows(*p, nsamps_out);
+  } else if (flags & DD_SUBBAND) {
+    if (p->sb_chans <= 0) return DD_ERR_INVALID_ARG;
+    dd_status s = prepare_subband(*p);
+    if (s != DD_OK) return s;
+    *rows = nsamps_out + p->sb_max_delay;
+  } else {
+    *rows = nsamps_out + p->max_delay;
+  }
   return DD_OK;
 }
 

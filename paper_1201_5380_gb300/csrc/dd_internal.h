@@ -223,6 +223,17 @@ struct Plan {
   std::vector<TimedLaunch> timed;
   double timed_ms[2] = {0.0, 0.0};
   int64_t timed_n[2] = {0, 0};
+  // time-scrunching (Sec. 2.2): 0 = off, else the largest factor; trials at
+  // one factor form a level, run by a child plan at resolution s*dt
+  int scrunch_max = 0;
+  bool scr_dirty = true;
+  struct ScrLevel {
+    int s, d_lo, d_hi;
+    std::unique_ptr<Plan> plan;
+  };
+  std::vector<ScrLevel> scr_levels;
+  std::vector<int32_t> scr_factor;  // per trial
+  DevBuf d_scr;                     // scrunched input of the level being run
   // host-pointer execute: output copies overlap the next part's compute
   cudaStream_t copy_st = nullptr;
   std::vector<cudaEvent_t> part_ev;
@@ -267,6 +278,12 @@ struct ExecArgs {
   bool subband;
 };
 dd_status exec_device(Plan& p, const ExecArgs& a);
+// Time-scrunched direct transform (device pointers); input rows needed.
+dd_status exec_scrunch(Plan& p, const ExecArgs& a);
+dd_status prepare_scrunch(Plan& p);
+int64_t scrunch_input_rows(const Plan& p, int64_t nsamps_out);
+dd_status build_delays(Plan& p);
+void plan_init_band(Plan& p, int nchans, double dt, double f0, double df);
 
 // Build the segments and launch parameters for a direct transform over an
 // already staged image (used by execute, streams and batches).

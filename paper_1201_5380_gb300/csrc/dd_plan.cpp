@@ -88,7 +88,7 @@ static double partial_delay(double f0, double df, double dt, int c) {
   return (kDispersionConst / dt) * (1.0 / (f * f) - 1.0 / (f0 * f0));
 }
 
-static dd_status build_delays(Plan& p) {
+dd_status build_delays(Plan& p) {
   const int n = ndm(p);
   std::vector<double> dT(p.nchans);
   for (int c = 0; c < p.nchans; ++c) dT[c] = partial_delay(p.f0, p.df, p.dt, c);
@@ -113,6 +113,7 @@ static dd_status build_delays(Plan& p) {
   p.delays_dirty = true;
   p.sb_dirty = true;
   drop_stage_tabs(p, 7);
+  p.scr_dirty = true;
   return DD_OK;
 }
 
@@ -303,6 +304,20 @@ Tuning tuning_for(const Tuning& t, int fmt) {
   return r;
 }
 
+void plan_init_band(Plan& p, int nchans, double dt, double f0, double df) {
+  p.nchans = nchans;
+  p.dt = dt;
+  p.f0 = f0;
+  p.df = df;
+  p.mask.assign(nchans, 1);
+  if (cudaGetDevice(&p.device) != cudaSuccess) p.device = 0;
+  cudaGetLastError();
+  if (cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device) !=
+      cudaSuccess)
+    p.num_sms = 0;
+  cudaGetLastError();
+}
+
 int tile_cfg_index(const Tuning& t0) {
   const Tuning t = t0.words_per_lane > 0 ? t0 : tuning_for(t0, FMT_NIB);
   for (int i = 0; i < kNumTileCfgs; ++i) {
@@ -342,17 +357,7 @@ dd_status dd_plan_create(dd_plan* out, int nchans, double dt_s, double f0_mhz, d
   if (!band_ok(nchans, dt_s, f0_mhz, df_mhz)) return DD_ERR_INVALID_ARG;
   Plan* p = new (std::nothrow) Plan();
   if (!p) return DD_ERR_OOM;
-  p->nchans = nchans;
-  p->dt = dt_s;
-  p->f0 = f0_mhz;
-  p->df = df_mhz;
-  p->mask.assign(nchans, 1);
-  if (cudaGetDevice(&p->device) != cudaSuccess) p->device = 0;
-  cudaGetLastError();
-  if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) !=
-      cudaSuccess)
-    p->num_sms = 0;
-  cudaGetLastError();
+  plan_init_band(*p, nchans, dt_s, f0_mhz, df_mhz);
   *out = reinterpret_cast<dd_plan>(p);
   return DD_OK;
 }
@@ -414,6 +419,7 @@ dd_status dd_plan_set_killmask(dd_plan plan, const uint8_t* mask) {
   std::lock_guard<std::mutex> lk(p->mu);
   for (int c = 0; c < p->nchans; ++c) p->mask[c] = mask ? (mask[c] ? 1 : 0) : 1;
   p->mask_dirty = true;
+  p->scr_dirty = true;
   return DD_OK;
 }
 
@@ -467,6 +473,7 @@ dd_status dd_plan_set_tuning(dd_plan plan, int dms_per_block, int cc, int words)
       found = true;
   if (!found) return DD_ERR_INVALID_ARG;
   p->tune = t;
+  p->scr_dirty = true;
   return DD_OK;
 }
 

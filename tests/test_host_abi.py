@@ -142,3 +142,33 @@ def test_server_api_validates_without_a_gpu():
         dd.Server(arena_bytes=1 << 20, max_batch=33)
     with pytest.raises(dd.DedispError):
         dd.Server(arena_bytes=1 << 20)             # no device to bind
+
+
+@pytest.mark.parametrize("band,hi", [(configs.SURVEY, 1000.0), (configs.FORMAT_SWEEP, 2000.0)])
+def test_scrunch_factors_match_oracle(orc, band, hi):
+    p = dd.Plan(band["nchans"], band["dt"], band["f0"], band["df"], dm_rule=dict(lo=0.0, hi=hi))
+    assert np.all(p.scrunch_factors == 1)          # off by default
+    p.set_scrunch(16)
+    ref = orc.scrunch_factors(p.dms, band["f0"], band["df"], band["dt"], 16)
+    assert np.array_equal(p.scrunch_factors, ref)
+    p.set_scrunch(4)
+    assert p.scrunch_factors.max() == 4
+
+
+def test_scrunch_input_rows_and_validation(orc):
+    c = configs.SURVEY
+    p = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
+    with pytest.raises(dd.DedispError):
+        p.set_scrunch(3)
+    with pytest.raises(dd.DedispError):
+        p.input_rows(1000, scrunch=True)           # scrunching not enabled
+    p.set_scrunch(16)
+    G = 10000
+    fac = p.scrunch_factors
+    need = 0
+    for s in sorted(set(fac.tolist())):
+        dms = p.dms[fac == s]
+        m = int(orc.delay_table(c["nchans"], c["f0"], c["df"], c["dt"] * s, dms).max())
+        need = max(need, s * (G // s + m))
+    assert p.input_rows(G, scrunch=True) == need
+    assert p.input_rows(G) == G + p.max_delay
