@@ -217,6 +217,16 @@ def direct_points_f32(data, delays, dsel, tsel, mask=None):
     return out, ab
 
 
+def scale_output(sums, nchans, vmax, bits) -> np.ndarray:
+    """Scaled low-bit output (Sec. 4.3 states only that the final output can
+    use fewer bits): keep the top `bits` bits of the range a sum can reach,
+    nchans * vmax: min(sum >> shift, 2^bits - 1), shift = max(0,
+    bitlen(nchans * vmax) - bits)."""
+    shift = max(0, int(nchans * vmax).bit_length() - bits)
+    out = np.minimum(np.asarray(sums, dtype=np.uint64) >> np.uint64(shift), (1 << bits) - 1)
+    return out.astype(np.uint8 if bits == 8 else np.uint16 if bits == 16 else np.uint32)
+
+
 def diagonal_dm(f0, df, dt) -> float:
     """Sec. 2.2: DM at which the smallest per-channel delay step is 1 sample."""
     return float(_load().orc_diagonal_dm(f0, df, dt))
