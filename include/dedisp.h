@@ -137,6 +137,17 @@ dd_status dd_plan_set_subband(dd_plan plan, int chans_per_subband,
  * Nominal trials stay exact either way. */
 dd_status dd_plan_set_subband_alignment(dd_plan plan, int centred);
 
+/* Bits per output sample of dd_execute: 32 (exact uint32 sums, the
+ * default), or 16 / 8 for the scaled low-bit output of Sec. 4.3.  The paper
+ * gives no scaling rule; here a scaled sample is
+ *   min(sum >> shift, 2^bits - 1),  shift = max(0, bitlen(N_nu * max) - bits),
+ * with max the largest input sample (2^nbits - 1) and bitlen(x) the number
+ * of bits of x: the top bits of the range the sum can reach, a plain
+ * integer operation.  Rows are then uint16 / uint8 with out_row_stride_elems
+ * in those elements.  Integer input only; not with DD_SCRUNCH, streams,
+ * batches, the server or dd_execute_noalloc (they take uint32 plans). */
+dd_status dd_plan_set_output_bits(dd_plan plan, int bits);
+
 /* Time-scrunching (Sec. 2.2): trials beyond twice the diagonal DM (where
  * the top two channels' delays differ by one sample) are dedispersed at
  * half the time resolution, at a quarter beyond four times it, and so on up

@@ -53,6 +53,7 @@ def _load_lib():
         "dd_plan_set_subband": (I, [P, I, I]),
         "dd_plan_set_subband_alignment": (I, [P, I]),
         "dd_plan_set_scrunch": (I, [P, I]),
+        "dd_plan_set_output_bits": (I, [P, I]),
         "dd_plan_get_scrunch_factors": (I, [P, P]),
         "dd_plan_get_input_rows": (I, [P, I64, ctypes.c_uint, pp(I64)]),
         "dd_plan_set_tuning": (I, [P, I, I, I]),
@@ -217,6 +218,11 @@ class Plan:
         if centred is not None:
             self.set_subband_alignment(centred)
 
+    def set_output_bits(self, bits):
+        """Output sample width of execute: 32 (exact), or 16 / 8 (scaled)."""
+        _check(_lib.dd_plan_set_output_bits(self._h, int(bits)), "dd_plan_set_output_bits")
+        self.out_bits = int(bits)
+
     def set_scrunch(self, max_factor):
         """Time-scrunching (Sec. 2.2) up to max_factor (power of two <= 16;
         0 turns it off); execute with scrunch=True."""
@@ -318,12 +324,12 @@ class Plan:
         if idev != odev:
             raise ValueError("input and output must both be on the device or both on the host")
         esize = out.element_size() if _is_torch(out) else out.itemsize
-        if esize != 4:
-            raise ValueError("output elements must be 32-bit")
+        if esize * 8 != getattr(self, "out_bits", 32):
+            raise ValueError("output elements must be %d-bit" % getattr(self, "out_bits", 32))
         flags = ((DD_DEVICE_PTRS if idev else 0) | (DD_SUBBAND if subband else 0) |
                  (DD_SCRUNCH if scrunch else 0))
         _check(_lib.dd_execute(self._h, int(nsamps_out), ip, int(nbits), int(istride), op,
-                               int(ostride // 4), _stream_ptr(stream), flags), "dd_execute")
+                               int(ostride // esize), _stream_ptr(stream), flags), "dd_execute")
         return out
 
 

@@ -595,6 +595,47 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
           } else if (SPW == 2) {
             dst[0] = v[0] | (v[1 % SPW] << 16);
           }
+        } else if (OUTK == OUT_U32 && p.out_bits < 32) {
+          // scaled low-bit output: the top out_bits of the sum's range
+          const uint32_t cap = (1u << p.out_bits) - 1u;
+          uint32_t w[SPW];
+#pragma unroll
+          for (int e = 0; e < SPW; ++e) w[e] = min(v[e] >> p.out_shift, cap);
+          const int esz = p.out_bits >> 3;
+          char* const row = reinterpret_cast<char*>(S.out) +
+                            ((int64_t)grp * S.g_out + (int64_t)(d0 + slot) * S.out_stride + tw) *
+                                esz;
+          const bool full = p.vec_out && tw + SPW <= t_end;
+          if (esz == 2 && full && SPW >= 2) {
+            uint32_t u[SPW / 2 > 0 ? SPW / 2 : 1];
+#pragma unroll
+            for (int q = 0; q < SPW / 2; ++q) u[q] = w[2 * q] | (w[(2 * q + 1) % SPW] << 16);
+            if (SPW == 8)
+              *reinterpret_cast<uint4*>(row) = make_uint4(u[0], u[1 % (SPW / 2)],
+                                                          u[2 % (SPW / 2)], u[3 % (SPW / 2)]);
+            else if (SPW == 4)
+              *reinterpret_cast<uint2*>(row) = make_uint2(u[0], u[1 % (SPW / 2)]);
+            else
+              *reinterpret_cast<uint32_t*>(row) = u[0];
+          } else if (esz == 1 && full && SPW >= 4) {
+            uint32_t u[SPW / 4 > 0 ? SPW / 4 : 1];
+#pragma unroll
+            for (int q = 0; q < SPW / 4; ++q)
+              u[q] = w[4 * q] | (w[(4 * q + 1) % SPW] << 8) | (w[(4 * q + 2) % SPW] << 16) |
+                     (w[(4 * q + 3) % SPW] << 24);
+            if (SPW == 8)
+              *reinterpret_cast<uint2*>(row) = make_uint2(u[0], u[1 % (SPW / 4)]);
+            else
+              *reinterpret_cast<uint32_t*>(row) = u[0];
+          } else if (esz == 2) {
+#pragma unroll
+            for (int e = 0; e < SPW; ++e)
+              if (tw + e < t_end) reinterpret_cast<uint16_t*>(row)[e] = (uint16_t)w[e];
+          } else {
+#pragma unroll
+            for (int e = 0; e < SPW; ++e)
+              if (tw + e < t_end) reinterpret_cast<uint8_t*>(row)[e] = (uint8_t)w[e];
+          }
         } else {
           uint32_t* dst = out_g + (int64_t)(d0 + slot) * S.out_stride + tw;
           if (p.vec_out && SPW >= 4 && tw + SPW <= t_end) {

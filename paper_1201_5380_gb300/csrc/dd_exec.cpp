@@ -236,6 +236,15 @@ void drop_stage_tabs(Plan& p, int kind_mask) {
   }
 }
 
+// Bytes per output element of a launch, and whether every output row and
+// tile start is 16-byte aligned (vector stores).
+int out_elem_bytes(const Plan& p, int outk) {
+  return outk == OUT_U32 && p.out_bits < 32 ? p.out_bits / 8 : 4;
+}
+bool out_vec_ok(const void* out, int64_t stride_elems, int esz) {
+  return !(reinterpret_cast<uintptr_t>(out) & 15) && !((stride_elems * esz) & 15);
+}
+
 // Channels per chunk for a launch whose largest staging spread is `spread`:
 // a power of two, at most two address-table entries per thread, and both
 // staging buffers within the shared-memory budget (0 if nothing fits).
@@ -302,6 +311,17 @@ static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector
   lp.f2 = f2;
   lp.n_items = items;
   lp.vec_out = vec_out ? 1 : 0;
+  // scaled low-bit output (Sec. 4.3): keep the top out_bits of the range a
+  // sum can reach, nchan * vmax
+  lp.out_bits = 32;
+  lp.out_shift = 0;
+  if (outk == OUT_U32 && p.out_bits < 32) {
+    const uint64_t top = (uint64_t)std::max(nchan_max, 1) * (uint64_t)std::max(vmax, 1);
+    int bl = 0;
+    while (bl < 64 && (top >> bl) != 0) ++bl;
+    lp.out_bits = p.out_bits;
+    lp.out_shift = std::max(0, bl - p.out_bits);
+  }
   // staging tables of each segment for this geometry
   {
     size_t i = 0;
@@ -371,7 +391,7 @@ dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
     s.seg.n_groups = 1;
     s.seg.ndm_last = j.ndm;
     if (lo > kPad) return DD_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(j.out) & 15) || (j.out_stride & 3)) vec = false;
+    if (!out_vec_ok(j.out, j.out_stride, out_elem_bytes(p, outk))) vec = false;
     s.kind = 0;
     s.owner = const_cast<Plan*>(j.plan);
     const std::vector<int32_t>& bl = j.plan->blocks_B[bi];
@@ -533,12 +553,13 @@ static dd_status exec_direct_host_out(Plan& p, const ExecArgs& a, int fmt, void*
     // rows of trials [starts[b0], starts[b1]) are final: copy them out
     // (row by row pitch: the caller's padding past nsamps is not written)
     const int64_t d0 = starts[b0], d1 = starts[b1];
-    const size_t off = (size_t)(d0 * a.out_stride) * 4;
-    const size_t pitch = (size_t)a.out_stride * 4;
+    const int esz = out_elem_bytes(p, fmt == FMT_F32 ? OUT_F32 : OUT_U32);
+    const size_t off = (size_t)(d0 * a.out_stride) * esz;
+    const size_t pitch = (size_t)a.out_stride * esz;
     if ((e = cudaStreamWaitEvent(p.copy_st, p.part_ev[q], 0)) != cudaSuccess ||
         (e = cudaMemcpy2DAsync(static_cast<uint8_t*>(host_out) + off, pitch,
                                static_cast<const uint8_t*>(a.out) + off, pitch,
-                               (size_t)a.nsamps_out * 4, (size_t)(d1 - d0),
+                               (size_t)a.nsamps_out * esz, (size_t)(d1 - d0),
                                cudaMemcpyDeviceToHost, p.copy_st)) != cudaSuccess)
       return cuda_status(e);
   }
@@ -660,7 +681,7 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
     sp.src = TabSrc{p.sb_d2.data(), (int64_t)p.sb_dms * nsb, nsb, nsb, ng,
                     p.sb2_blk_B[bi].data(), p.sb2_nblk_B[bi], lo2};
   }
-  const bool vec = !(reinterpret_cast<uintptr_t>(a.out) & 15) && !(a.out_stride & 3);
+  const bool vec = out_vec_ok(a.out, a.out_stride, out_elem_bytes(p, OUT_U32));
   LaunchPlan L2;
   s = finish_launch(p, fmt2, OUT_U32, (int)std::min<int64_t>(vmax1, INT_MAX), specs, vec, &L2);
   if (s != DD_OK) return s;
@@ -716,7 +737,9 @@ extern "C" dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void* in
   a.st = static_cast<cudaStream_t>(cuda_stream);
   a.subband = sub;
   const size_t in_bytes = (size_t)(rows - 1) * in_row_stride + row_bytes;
-  const size_t out_bytes = (size_t)((int64_t)(ndm(*p) - 1) * out_stride + nsamps_out) * 4;
+  const int esz = p->out_bits / 8;
+  if (esz != 4 && (in_nbits == 32 || scr)) return DD_ERR_INVALID_ARG;
+  const size_t out_bytes = (size_t)((int64_t)(ndm(*p) - 1) * out_stride + nsamps_out) * esz;
   if (flags & DD_DEVICE_PTRS) {
     if (!device_range_ok(in, in_bytes)) return DD_ERR_INPUT_TOO_SHORT;
     if (!device_range_ok(out, out_bytes)) return DD_ERR_INVALID_ARG;
@@ -735,11 +758,19 @@ extern "C" dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void* in
   if (!sub) return exec_direct_host_out(*p, a, fmt, out);
   dd_status s = exec_device(*p, a);
   if (s != DD_OK) return s;
-  if ((e = cudaMemcpy2DAsync(out, (size_t)out_stride * 4, p->d_out.p, (size_t)out_stride * 4,
-                             (size_t)nsamps_out * 4, (size_t)ndm(*p), cudaMemcpyDeviceToHost,
-                             a.st)) != cudaSuccess)
+  if ((e = cudaMemcpy2DAsync(out, (size_t)out_stride * esz, p->d_out.p,
+                             (size_t)out_stride * esz, (size_t)nsamps_out * esz,
+                             (size_t)ndm(*p), cudaMemcpyDeviceToHost, a.st)) != cudaSuccess)
     return cuda_status(e);
   if ((e = cudaStreamSynchronize(a.st)) != cudaSuccess) return cuda_status(e);
+  return DD_OK;
+}
+
+extern "C" dd_status dd_plan_set_output_bits(dd_plan plan, int bits) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p || (bits != 8 && bits != 16 && bits != 32)) return DD_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(p->mu);
+  p->out_bits = bits;
   return DD_OK;
 }
 

@@ -102,6 +102,8 @@ struct LaunchParams {
   // launch; null = static striding by the grid size
   unsigned long long* next_item;
   int32_t vec_out;   // 1 if every output row/tile start is 16-byte aligned
+  int32_t out_bits;  // 32, or 16 / 8: scaled output (OUT_U32 launches)
+  int32_t out_shift; // scaled output = min(sum >> out_shift, 2^out_bits - 1)
   int32_t pad_;
 };
 
@@ -225,6 +227,7 @@ struct Plan {
   int64_t timed_n[2] = {0, 0};
   // time-scrunching (Sec. 2.2): 0 = off, else the largest factor; trials at
   // one factor form a level, run by a child plan at resolution s*dt
+  int out_bits = 32;  // bits per output sample of dd_execute (8, 16 or 32)
   int scrunch_max = 0;
   bool scr_dirty = true;
   struct ScrLevel {
@@ -328,6 +331,8 @@ void make_blocks(const int32_t* delays, int ndm, int nchans, int stride, int B,
 // 220 KB of shared memory.
 constexpr int32_t kSpreadBudget = 4000;
 int time_tile(int fmt, const Tuning& t);
+int out_elem_bytes(const Plan& p, int outk);
+bool out_vec_ok(const void* out, int64_t stride_elems, int esz);
 // Channels per staged chunk that plan p's tiling gives a launch whose
 // largest staging spread is `spread` (0 if it cannot be staged).
 int chunk_channels(const Plan& p, int fmt, int32_t spread);

@@ -57,6 +57,7 @@ extern "C" dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const 
   const int fmt = fmt_for_nbits(in_nbits);
   if (fmt < 0) return DD_ERR_UNSUPPORTED_NBITS;
   if (p->dms.empty()) return DD_ERR_NO_DM_LIST;
+  if (p->out_bits != 32) return DD_ERR_INVALID_ARG;
   const int64_t row_bytes =
       in_nbits == 32 ? (int64_t)p->nchans * 4 : ((int64_t)p->nchans * in_nbits + 7) / 8;
   if (in_row_stride < row_bytes) return DD_ERR_INVALID_ARG;

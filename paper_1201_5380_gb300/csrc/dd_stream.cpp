@@ -103,6 +103,7 @@ dd_status dd_stream_create(dd_stream* out, dd_plan plan, int nbits, int64_t max_
   if (!p || max_gulp <= 0) return DD_ERR_INVALID_ARG;
   if (fmt_for_nbits(nbits) < 0) return DD_ERR_UNSUPPORTED_NBITS;
   if (p->dms.empty()) return DD_ERR_NO_DM_LIST;
+  if (p->out_bits != 32) return DD_ERR_INVALID_ARG;  // streams write uint32 rows
   dd_stream h = new (std::nothrow) dd_stream_s();
   if (!h) return DD_ERR_OOM;
   StreamState& s = h->s;
@@ -133,6 +134,7 @@ dd_status dd_stream_push(dd_stream h, const void* in, int64_t n_in, int64_t in_s
   *nsamps_out = 0;
   if (n_in > s.max_gulp || in_stride < s.row_bytes || out_stride < n_in) return DD_ERR_INVALID_ARG;
   if (p.max_delay + s.max_gulp > s.cap_rows) return DD_ERR_INVALID_ARG;  // plan changed
+  if (p.out_bits != 32) return DD_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(p.mu);
   dd_status r = ensure_device_tables(p);
   if (r != DD_OK) return r;
@@ -245,7 +247,8 @@ dd_status dd_batch_clear(dd_batch b) {
 dd_status dd_batch_add(dd_batch b, dd_stream s, const void* in, int64_t n_in, int64_t in_stride,
                        void* out, int64_t out_stride) {
   if (!b || !s || !in || !out || n_in < 0) return DD_ERR_INVALID_ARG;
-  if (n_in > s->s.max_gulp || in_stride < s->s.row_bytes || out_stride < n_in)
+  if (n_in > s->s.max_gulp || in_stride < s->s.row_bytes || out_stride < n_in ||
+      s->s.plan->out_bits != 32)
     return DD_ERR_INVALID_ARG;
   if (!b->items.empty() && b->items[0].stream->s.nbits != s->s.nbits) return DD_ERR_INVALID_ARG;
   for (const BatchItem& it : b->items)

@@ -204,3 +204,48 @@ def test_integer_add_probe_runs():
     torch_cuda()
     rate, ms = dd.probe_int_add(1 << 14)
     assert rate > 1e12 and ms > 0
+
+
+@pytest.mark.parametrize("bits", [8, 16])
+def test_scaled_output_bit_exact(orc, bits):
+    torch = torch_cuda()
+    plan = _survey_plan(step=15)
+    plan.set_output_bits(bits)
+    nsamps = 2100
+    rows = nsamps + plan.max_delay
+    x = synth.uniform_packed(51, 0, rows, 1024, 2)
+    ref = orc.scale_output(orc.direct(x, 2, 1024, nsamps, odelays(orc, plan)), 1024, 3, bits)
+    dt = torch.uint8 if bits == 8 else torch.int16
+    for pad in (0, 5):                 # aligned rows (vector stores) and ragged rows
+        out = torch.zeros((plan.dm_count, nsamps + pad), dtype=dt, device="cuda")
+        plan.execute(torch.from_numpy(x).cuda(), 2, nsamps, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(ref.dtype)
+        assert np.array_equal(got[:, :nsamps], ref)
+        assert np.all(got[:, nsamps:] == 0)
+    host = np.zeros((plan.dm_count, nsamps + 3), dtype=ref.dtype)
+    plan.execute(x, 2, nsamps, host)   # host pointers (parts copied out)
+    assert np.array_equal(host[:, :nsamps], ref)
+
+
+def test_scaled_output_subband_bit_exact(orc):
+    torch = torch_cuda()
+    c = configs.SURVEY
+    full = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
+    plan = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dms=full.dms[::10], subband=(32, 16))
+    plan.set_output_bits(8)
+    nsamps = 1500
+    x = synth.uniform_packed(52, 0, nsamps + plan.subband_max_delay, 1024, 2)
+    ref = orc.scale_output(orc.subband(x, 2, 1024, 32, 16, odelays(orc, plan), nsamps), 1024, 3, 8)
+    out = torch.zeros((plan.dm_count, nsamps), dtype=torch.uint8, device="cuda")
+    plan.execute(torch.from_numpy(x).cuda(), 2, nsamps, out, subband=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_scaled_output_rejected_where_uint32_rows_are_required():
+    torch_cuda()
+    plan = dd.Plan(64, 64e-6, 1500.0, -1.0, dms=[0.0, 10.0])
+    plan.set_output_bits(8)
+    with pytest.raises(dd.DedispError):
+        dd.Stream(plan, 2, 1000)

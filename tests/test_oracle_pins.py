@@ -441,3 +441,14 @@ def test_scrunched_trial_recovers_an_aligned_pulse(orc):
     out, _ = orc.direct_scrunched(x, 8, 400, f0, df, dt, [dm])
     assert out[0, t0] == out[0, t0 + 1] == 3 * 8 * fac
     assert out[0].sum() == 2 * 3 * 8 * fac
+
+
+def test_scaled_output_keeps_the_top_bits(orc):
+    # 1024 channels of 2-bit samples reach 3072 (12 bits): 8-bit output drops
+    # the 4 low bits, 16-bit output drops none
+    s = np.array([0, 15, 16, 17, 3071, 3072], dtype=np.uint32)
+    assert orc.scale_output(s, 1024, 3, 8).tolist() == [0, 0, 1, 1, 191, 192]
+    assert orc.scale_output(s, 1024, 3, 16).tolist() == s.tolist()
+    assert orc.scale_output(s, 1024, 3, 8).dtype == np.uint8
+    # 64 channels of 8-bit samples reach 16320 (14 bits): shift 6 for 8-bit
+    assert orc.scale_output(np.array([16320, 63, 64]), 64, 255, 8).tolist() == [255, 0, 1]
