@@ -495,6 +495,45 @@ def run_scrunch(a, x, G, plain_ms):
             "work_vs_direct": float(np.sum(1.0 / fac) / fac.size)}
 
 
+def run_scaled(a, x, G):
+    """Scaled 8-bit output (Sec. 4.3) on the survey gulp: the device step and
+    the end-to-end step through dd_execute with host buffers (the output
+    copy shrinks 4x)."""
+    import torch
+    import paper_1201_5380_gb300 as dd
+
+    c = configs.SURVEY
+    plan = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
+    plan.set_output_bits(8)
+    ndm = plan.dm_count
+    d_in = torch.from_numpy(x).cuda()
+    out = torch.empty((ndm, G), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        plan.execute(d_in, 2, G, out)
+    torch.cuda.synchronize()
+    reps = 10
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(reps):
+        plan.execute(d_in, 2, G, out)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    h_in = torch.empty(x.shape, dtype=torch.uint8, pin_memory=True)
+    h_in.numpy()[:] = x
+    h_out = torch.empty((ndm, G), dtype=torch.uint8, pin_memory=True)
+    plan.execute(h_in.numpy(), 2, G, h_out.numpy())
+    t0 = time.perf_counter()
+    for _ in range(5):
+        plan.execute(h_in.numpy(), 2, G, h_out.numpy())
+    e2e_ms = (time.perf_counter() - t0) / 5 * 1e3
+    units = float(c["nchans"]) * ndm * G
+    return {"workload": "the survey gulp with 8-bit scaled output rows",
+            "ms_per_step": ms, "value": units / (ms / 1e3) / 1e9, "unit": UNIT,
+            "e2e": {"value": units / (e2e_ms / 1e3) / 1e9, "ms_per_step": e2e_ms,
+                    "d2h_bytes_per_step": ndm * G}}
+
+
 def run_graph(a):
     """Steady-state streaming of the 13 serving beams at 2^14 samples per
     gulp (device buffers): per gulp, host time to submit the work (median,
@@ -673,6 +712,7 @@ def run_ours(a, rank, world, local_rank):
     }
     if rank == 0 and world == 1 and not a.no_subband and not a.gulp:
         line["scrunch"] = run_scrunch(a, x, G, ms_step)
+        line["scaled_output"] = run_scaled(a, x, G)
         line["subband"] = run_subband(a, x, plan, out, G)
         line["subband"]["speedup_vs_direct_kernels"] = (
             k_ms / line["subband"]["early_edge"]["kernels_ms"])

@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
           } else if (SPW == 2) {
             dst[0] = v[0] | (v[1 % SPW] << 16);
           }
-        } else if (OUTK == OUT_U32 && p.out_bits < 32) {
+        } else if (OUTK == OUT_NARROW) {
           // scaled low-bit output: the top out_bits of the sum's range
           const uint32_t cap = (1u << p.out_bits) - 1u;
           uint32_t w[SPW];

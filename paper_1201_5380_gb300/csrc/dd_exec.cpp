@@ -321,6 +321,7 @@ static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector
     while (bl < 64 && (top >> bl) != 0) ++bl;
     lp.out_bits = p.out_bits;
     lp.out_shift = std::max(0, bl - p.out_bits);
+    L->outk = OUT_NARROW;
   }
   // staging tables of each segment for this geometry
   {
@@ -343,7 +344,7 @@ static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector
   }
   L->smem = dedisp_smem_bytes(fmt, cfg, cc, nww);
   int per_sm = 0;
-  cudaError_t e = dedisp_max_blocks_per_sm(fmt, outk, wide, cfg, L->smem, &per_sm);
+  cudaError_t e = dedisp_max_blocks_per_sm(fmt, L->outk, wide, cfg, L->smem, &per_sm);
   if (e != cudaSuccess) return cuda_status(e);
   if (per_sm < 1) return DD_ERR_INVALID_ARG;
   const int64_t resident = (int64_t)per_sm * std::max(1, p.num_sms);

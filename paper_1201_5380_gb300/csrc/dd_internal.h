@@ -30,7 +30,9 @@ namespace dd {
 //   FMT_F32  32-bit float, 1 sample/word, float input
 // ---------------------------------------------------------------------------
 enum Fmt { FMT_NIB = 0, FMT_BYTE = 1, FMT_HALF = 2, FMT_U32 = 3, FMT_F32 = 4 };
-enum OutKind { OUT_U32 = 0, OUT_F32 = 1, OUT_HALFIMG = 2 };
+// OUT_NARROW: scaled uint8/uint16 rows (LaunchParams::out_bits, out_shift),
+// a separate instantiation so the uint32 kernel's code is untouched.
+enum OutKind { OUT_U32 = 0, OUT_F32 = 1, OUT_HALFIMG = 2, OUT_NARROW = 3 };
 
 constexpr int kPad = 32;  // image samples before time 0 (multiple of 4*SPW)
 

@@ -10,6 +10,9 @@ cudaError_t dispatch_half(int outk, bool wide, int cfg, const LaunchParams* p, i
                 : dispatch_cfg<FMT_HALF, OUT_U32, false>(cfg, p, grid, smem, st, occ);
   if (outk == OUT_HALFIMG && !wide)
     return dispatch_cfg<FMT_HALF, OUT_HALFIMG, false>(cfg, p, grid, smem, st, occ);
+  if (outk == OUT_NARROW)
+    return wide ? dispatch_cfg<FMT_HALF, OUT_NARROW, true>(cfg, p, grid, smem, st, occ)
+                : dispatch_cfg<FMT_HALF, OUT_NARROW, false>(cfg, p, grid, smem, st, occ);
   return cudaErrorInvalidValue;
 }
 

@@ -10,6 +10,9 @@ cudaError_t dispatch_nib(int outk, bool wide, int cfg, const LaunchParams* p, in
                 : dispatch_cfg<FMT_NIB, OUT_U32, false>(cfg, p, grid, smem, st, occ);
   if (outk == OUT_HALFIMG && !wide)
     return dispatch_cfg<FMT_NIB, OUT_HALFIMG, false>(cfg, p, grid, smem, st, occ);
+  if (outk == OUT_NARROW)
+    return wide ? dispatch_cfg<FMT_NIB, OUT_NARROW, true>(cfg, p, grid, smem, st, occ)
+                : dispatch_cfg<FMT_NIB, OUT_NARROW, false>(cfg, p, grid, smem, st, occ);
   return cudaErrorInvalidValue;
 }
 
