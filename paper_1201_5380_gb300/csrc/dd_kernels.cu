@@ -114,6 +114,64 @@ __global__ void __launch_bounds__(256) k_corner_turn(const uint8_t* __restrict__
   }
 }
 
+// 2-bit input, 1024-byte-aligned rows: the common survey case, specialised.
+// Block = 256 threads over 128 channels (32 input bytes per row) x 256 rows
+// (32 image words).  Phase 1: each thread loads one row's 32 bytes with two
+// 16-byte loads and stores them transposed (byte column major), so the 8
+// rows of one image word of a byte column are 8 consecutive bytes.  Phase 2:
+// a warp owns one byte column (4 channels) x 32 image words; a lane reads its
+// 8 bytes with one 64-bit load and spreads each channel's 2-bit fields to
+// 4-bit lanes: (x >> 2k) & 0x03.. keeps channel k in every byte, folding the
+// odd bytes into the even bytes' high nibbles and keeping bytes 0, 2, 4, 6
+// gives the word.  Requires in, in_stride 16-byte aligned, nchans % 128 == 0.
+__global__ void __launch_bounds__(256) k_corner_turn_2bit(const uint8_t* __restrict__ in,
+                                                          int64_t in_stride, int64_t t_begin,
+                                                          int64_t nrows_valid, int nchans,
+                                                          const uint8_t* __restrict__ mask,
+                                                          uint32_t* __restrict__ img,
+                                                          int64_t row_words, int64_t words) {
+  constexpr int ROWS = 256, COLS = 32, PITCH = ROWS + 8;  // bytes per byte-column row
+  __shared__ __align__(16) uint8_t tile[COLS * PITCH];
+  const int64_t w0 = (int64_t)blockIdx.x * 32;     // first image word
+  const int cb0 = blockIdx.y * 128;                // first channel
+  const int64_t r0 = t_begin + w0 * 8 - kPad;      // raw row of the block's first sample
+  {
+    const int rr = threadIdx.x;
+    const int64_t r = r0 + rr;
+    uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a;
+    if (r >= t_begin && r < t_begin + nrows_valid) {
+      const uint4* src = reinterpret_cast<const uint4*>(in + r * in_stride + cb0 / 4);
+      a = __ldg(src);
+      b = __ldg(src + 1);
+    }
+    const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) tile[(q * 4 + k) * PITCH + rr] = (uint8_t)(v[q] >> (8 * k));
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w = w0 + lane;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int col = warp * 4 + it;                 // byte column: channels 4*col .. +3
+    const uint2 x = *reinterpret_cast<const uint2*>(&tile[col * PITCH + lane * 8]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = cb0 + col * 4 + k;
+      const uint32_t lo = (x.x >> (2 * k)) & 0x03030303u;
+      const uint32_t hi = (x.y >> (2 * k)) & 0x03030303u;
+      // bytes 0..7 hold the samples; fold byte 2j+1 into byte 2j's high nibble
+      const uint32_t flo = lo | (lo >> 4);
+      const uint32_t fhi = hi | (hi >> 4);
+      uint32_t word = __byte_perm(flo, fhi, 0x6420);
+      if (mask && mask[c] == 0) word = 0u;
+      if (w < words) img[(int64_t)c * row_words + w] = word;
+    }
+  }
+}
+
 cudaError_t launch_corner_turn(int nbits, const uint8_t* in, int64_t in_stride, int64_t t_begin,
                                int64_t nrows_valid, int nchans, const uint8_t* mask,
                                uint32_t* img, int64_t row_words, int64_t words,
@@ -123,6 +181,13 @@ cudaError_t launch_corner_turn(int nbits, const uint8_t* in, int64_t in_stride, 
   dim3 grid((unsigned)((words + WB - 1) / WB), (unsigned)((nchans + CB - 1) / CB));
   if (grid.x == 0 || grid.y == 0) return cudaSuccess;
   if (grid.y > 65535) return cudaErrorInvalidValue;
+  if (nbits == 2 && nchans % 128 == 0 && !(reinterpret_cast<uintptr_t>(in) & 15) &&
+      !(in_stride & 15)) {
+    const dim3 g2((unsigned)((words + 31) / 32), (unsigned)(nchans / 128));
+    k_corner_turn_2bit<<<g2, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img,
+                                           row_words, words);
+    return cudaGetLastError();
+  }
   switch (nbits) {
     case 1: k_corner_turn<1><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, words); break;
     case 2: k_corner_turn<2><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, words); break;
