@@ -48,20 +48,25 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-subband", action="store_true")
+    ap.add_argument("--nbits", type=int, default=2, choices=[1, 2, 4, 8],
+                    help="input bits per sample (the survey workload is 2-bit)")
+    ap.add_argument("--dm-hi", type=float, default=1000.0,
+                    help="largest trial DM (the survey workload: 1000)")
     ap.add_argument("--gulp", type=int, default=0,
                     help="samples per gulp (default: the workload's 2^19); smaller values "
                          "are for profiler captures, not bench lines")
     return ap.parse_args()
 
 
-def _make_input(plan_dms, delays, G, max_delay):
+def _make_input(plan_dms, delays, G, max_delay, nbits=2):
     c = configs.SURVEY
     rows = G + max_delay
-    x = synth.uniform_packed(c["seed"], 0, rows, c["nchans"], 2)
+    x = synth.uniform_packed(c["seed"], 0, rows, c["nchans"], nbits)
     for p in c["pulses"]:
         k = int(np.argmin(np.abs(plan_dms - p["dm"])))
-        x = synth.inject_boxcar_packed(x, 2, c["nchans"], delays[k], p["t0"], p["width"],
-                                       p["value"])
+        if k < delays.shape[0] and p["t0"] + p["width"] + int(delays[k].max()) < rows:
+            x = synth.inject_boxcar_packed(x, nbits, c["nchans"], delays[k], p["t0"], p["width"],
+                                           (1 << nbits) - 1)
     return x
 
 
@@ -129,7 +134,7 @@ class ClockSampler:
 DEDISP_TRAFFIC_2E17 = 77.903616e6 + 569.380864e6
 
 
-def cpu_oracle_rate(x, delays, G, seconds):
+def cpu_oracle_rate(x, delays, G, seconds, nbits=2):
     """Time the CPU oracle (as it stands) on a bounded sample of the workload:
     trials evenly spaced over the list, all channels, a prefix of the gulp.
     Returns (Gchan*DM*samp/s, cores, description)."""
@@ -138,7 +143,7 @@ def cpu_oracle_rate(x, delays, G, seconds):
     nchans = delays.shape[1]
     probe_d = np.linspace(0, delays.shape[0] - 1, 8).astype(int)
     t0 = time.perf_counter()
-    oracle.direct(x, 2, nchans, 2048, delays[probe_d])
+    oracle.direct(x, nbits, nchans, 2048, delays[probe_d])
     dt = max(time.perf_counter() - t0, 1e-3)
     rate = 8 * 2048 * nchans / dt
     # the small probe underestimates the threaded rate: size a first sample
@@ -150,7 +155,7 @@ def cpu_oracle_rate(x, delays, G, seconds):
         ns = int(min(G, max(2048, want // (nchans * ntr))))
         sel = np.linspace(0, delays.shape[0] - 1, ntr).astype(int)
         t0 = time.perf_counter()
-        oracle.direct(x, 2, nchans, ns, delays[sel])
+        oracle.direct(x, nbits, nchans, ns, delays[sel])
         dt = time.perf_counter() - t0
         rate = float(ntr) * ns * nchans / max(dt, 1e-3)
         budget = seconds
@@ -168,10 +173,11 @@ def run_reference(a, rank, world):
     import oracle
     oracle.build()
     c = configs.SURVEY
-    dms = oracle.dm_list(c["nchans"], c["f0"], c["df"], c["dt"], 0.0, 1000.0)
+    dms = oracle.dm_list(c["nchans"], c["f0"], c["df"], c["dt"], 0.0, a.dm_hi)
     delays = oracle.delay_table(c["nchans"], c["f0"], c["df"], c["dt"], dms)
     G = c["nsamps"]
-    x = _make_input(dms, delays, G, int(delays.max()))
+    nb = a.nbits
+    x = _make_input(dms, delays, G, int(delays.max()), nb)
     nchans = c["nchans"]
     # each step: a bounded sample of the workload (evenly spaced trials, a
     # prefix of the gulp) sized to a few seconds of CPU work
@@ -179,11 +185,11 @@ def run_reference(a, rank, world):
     sel = np.linspace(0, delays.shape[0] - 1, ntr).astype(int)
     sub = delays[sel]
     for _ in range(a.warmup):
-        oracle.direct(x, 2, nchans, ns, sub)
+        oracle.direct(x, nb, nchans, ns, sub)
     times = []
     for _ in range(a.steps):
         t0 = time.perf_counter()
-        oracle.direct(x, 2, nchans, ns, sub)
+        oracle.direct(x, nb, nchans, ns, sub)
         times.append(time.perf_counter() - t0)
     T = sum(times)
     value = a.steps * ntr * ns * nchans / T / 1e9
@@ -193,8 +199,10 @@ def run_reference(a, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * T / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "nchans": nchans,
-                                        "ndm": int(delays.shape[0]), "gulp": G, "nbits": 2},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if (nb == 2 and a.dm_hi == 1000.0) else
+                   "survey band, %d-bit input, trial DMs 0-%g" % (nb, a.dm_hi),
+                   "nchans": nchans, "ndm": int(delays.shape[0]), "gulp": G, "nbits": nb},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                          "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -609,11 +617,12 @@ def run_ours(a, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     c = configs.SURVEY
     nchans, G = c["nchans"], (a.gulp or c["nsamps"])
-    plan = dd.Plan(nchans, c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0),
+    nb = a.nbits
+    plan = dd.Plan(nchans, c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=a.dm_hi),
                    gulp=G)
     ndm = plan.dm_count
     delays = plan.delay_table()
-    x = _make_input(plan.dms, delays, G, plan.max_delay)
+    x = _make_input(plan.dms, delays, G, plan.max_delay, nb)
     in_bytes = x.nbytes
     out_bytes = ndm * G * 4
     d_in = torch.from_numpy(x).to(dev)
@@ -621,7 +630,7 @@ def run_ours(a, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(a.warmup):
-        plan.execute(d_in, 2, G, out, stream=stream)
+        plan.execute(d_in, nb, G, out, stream=stream)
     torch.cuda.synchronize(dev)
     if plan.device_status() != 0:
         raise RuntimeError("device-side bound flag set during warm-up")
@@ -642,7 +651,7 @@ def run_ours(a, rank, world, local_rank):
     time.sleep(0.3)
     evs[0].record(stream)
     for i in range(a.steps):
-        plan.execute(d_in, 2, G, out, stream=stream)
+        plan.execute(d_in, nb, G, out, stream=stream)
         evs[i + 1].record(stream)
     torch.cuda.synchronize(dev)
     clocks = clk.stop()
@@ -661,11 +670,11 @@ def run_ours(a, rank, world, local_rank):
     h_in.numpy()[:] = x
     h_out = torch.empty((ndm, G), dtype=torch.int32, pin_memory=True)
     hin, hout = h_in.numpy(), h_out.numpy()
-    plan.execute(hin, 2, G, hout)
+    plan.execute(hin, nb, G, hout)
     barrier()
     t0 = time.perf_counter()
     for _ in range(a.e2e_steps):
-        plan.execute(hin, 2, G, hout)
+        plan.execute(hin, nb, G, hout)
     e2e_s = (time.perf_counter() - t0) / max(a.e2e_steps, 1)
     e2e_ms, e2e_value = replica_throughput(e2e_s * 1e3, units, world, dev)
     e2e_s = e2e_ms / 1e3
@@ -689,9 +698,12 @@ def run_ours(a, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nchans": nchans, "ndm": ndm, "gulp": G, "nbits": 2,
+        "config": {"workload": WORKLOAD if (nb == 2 and a.dm_hi == 1000.0) else
+                   "survey band, %d-bit input, trial DMs 0-%g" % (nb, a.dm_hi),
+                   "nchans": nchans, "ndm": ndm, "gulp": G, "nbits": nb,
                    "max_delay": plan.max_delay, "tuning": plan.get_tuning(),
-                   "l2": "inputs larger than L2 (139 MB in, 2.5 GB out per step); no flush",
+                   "l2": "inputs larger than L2 (%d MB in, %.1f GB out per step); no flush"
+                         % (in_bytes // 10**6, out_bytes / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "rtf": G * c["dt"] / (ms_step / 1e3),
         "step_ms_p5_p50_p95": [float(np.percentile(step_ms, q)) for q in (5, 50, 95)],
@@ -701,7 +713,8 @@ def run_ours(a, rank, world, local_rank):
         "kernels_ms_per_step": {"dedisp": k_ms, "corner_turn": ct_ms / max(ct_n, 1)},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12,
                      "unit": "Tadd/s", "frac": achieved / peak_adds,
-                     "traffic": DEDISP_TRAFFIC_2E17 * G / 131072.0,
+                     "traffic": (DEDISP_TRAFFIC_2E17 * G / 131072.0
+                                 if (nb == 2 and a.dm_hi == 1000.0) else None),
                      "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one "
                                        "ncu capture at 2^17 samples, scaled by the gulp "
                                        "(profiles/k_dedisp_survey_ncu_full.md)",
@@ -710,13 +723,14 @@ def run_ours(a, rank, world, local_rank):
                      "hbm_gbs_used": hbm},
         "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not a.no_subband and not a.gulp:
+    default = nb == 2 and a.dm_hi == 1000.0 and not a.gulp
+    if rank == 0 and world == 1 and not a.no_subband and default:
         line["scrunch"] = run_scrunch(a, x, G, ms_step)
         line["scaled_output"] = run_scaled(a, x, G)
         line["subband"] = run_subband(a, x, plan, out, G)
         line["subband"]["speedup_vs_direct_kernels"] = (
             k_ms / line["subband"]["early_edge"]["kernels_ms"])
-    if rank == 0 and world == 1 and not a.no_serving and not a.gulp:
+    if rank == 0 and world == 1 and not a.no_serving and default:
         del d_in, out
         torch.cuda.empty_cache()
         line["serving"] = run_serving(a)
@@ -725,7 +739,7 @@ def run_ours(a, rank, world, local_rank):
         import oracle
         oracle.build()
         oracle_delays = oracle.delay_table(nchans, c["f0"], c["df"], c["dt"], plan.dms)
-        v, cores, desc, secs = cpu_oracle_rate(x, oracle_delays, G, a.cpu_seconds)
+        v, cores, desc, secs = cpu_oracle_rate(x, oracle_delays, G, a.cpu_seconds, nb)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": desc, "seconds": secs}
     if rank == 0:
