@@ -130,8 +130,12 @@ class ClockSampler:
 # ------------------------------------------------------------ cpu oracle
 
 # DRAM bytes (read + write) of one dedispersion launch on the survey band at
-# 2^17 output samples, from ncu; the traffic grows in proportion to the gulp.
-DEDISP_TRAFFIC_2E17 = 77.903616e6 + 569.380864e6
+# 2^17 output samples, from ncu, per (input bits, largest trial DM), with the
+# summary that holds the capture; the traffic grows in proportion to the gulp.
+DEDISP_TRAFFIC_2E17 = {
+    (2, 1000.0): (77.903616e6 + 569.380864e6, "profiles/k_dedisp_survey_ncu_full.md"),
+    (8, 2000.0): (524.051968e6 + 731.931904e6, "profiles/k_dedisp_8bit_dm2000_ncu_full.md"),
+}
 
 
 def cpu_oracle_rate(x, delays, G, seconds, nbits=2):
@@ -693,6 +697,7 @@ def run_ours(a, rank, world, local_rank):
     except OSError:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
+    traffic = DEDISP_TRAFFIC_2E17.get((nb, float(a.dm_hi)))
     byte_floor_ms = (in_bytes + out_bytes) / (hbm * 1e9) * 1e3
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -713,11 +718,11 @@ def run_ours(a, rank, world, local_rank):
         "kernels_ms_per_step": {"dedisp": k_ms, "corner_turn": ct_ms / max(ct_n, 1)},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12,
                      "unit": "Tadd/s", "frac": achieved / peak_adds,
-                     "traffic": (DEDISP_TRAFFIC_2E17 * G / 131072.0
-                                 if (nb == 2 and a.dm_hi == 1000.0) else None),
+                     "traffic": traffic[0] * G / 131072.0 if traffic else None,
                      "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one "
                                        "ncu capture at 2^17 samples, scaled by the gulp "
-                                       "(profiles/k_dedisp_survey_ncu_full.md)",
+                                       "(%s)" % (traffic[1] if traffic else "none for "
+                                                 "this workload"),
                      "peak_source": "measured integer-add probe (dd_probe_int_add)",
                      "byte_floor_ms": byte_floor_ms, "compute_floor_ms": units / peak_adds * 1e3,
                      "hbm_gbs_used": hbm},
