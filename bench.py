@@ -48,6 +48,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-subband", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the format sweep (1/4/8-bit and float input)")
     ap.add_argument("--nbits", type=int, default=2, choices=[1, 2, 4, 8],
                     help="input bits per sample (the survey workload is 2-bit)")
     ap.add_argument("--dm-hi", type=float, default=1000.0,
@@ -546,6 +548,61 @@ def run_scaled(a, x, G):
                     "d2h_bytes_per_step": ndm * G}}
 
 
+def run_format_sweep(a):
+    """The format sweep (1024-channel band, trials 0-2000 by the smearing
+    rule): dedispersion kernel time per launch for 1-, 4- and 8-bit and float
+    input at 2^17 and 2^20 samples.  The kernels do the same integer adds
+    whatever the sample values, so these timing-only inputs are drawn on the
+    device (uniform bytes, N(0,1) floats); the formats' parity is tested on
+    inputs from the seeded generators."""
+    import torch
+    import paper_1201_5380_gb300 as dd
+
+    c = configs.FORMAT_SWEEP
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(c["seed"])
+    peak, _ = dd.probe_int_add(1 << 16)
+    rows_out = []
+    for G in c["nsamps_list"]:
+        plan = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"],
+                       dm_rule=dict(lo=c["dms"]["lo"], hi=c["dms"]["hi"]), gulp=G)
+        ndm = plan.dm_count
+        rows = G + plan.max_delay
+        for nb in c["nbits_list"]:
+            if nb == 32:
+                d_in = torch.randn((rows, c["nchans"]), generator=gen, device="cuda")
+                out = torch.empty((ndm, G), dtype=torch.float32, device="cuda")
+            else:
+                d_in = torch.randint(0, 256, (rows, c["nchans"] * nb // 8), generator=gen,
+                                     dtype=torch.uint8, device="cuda")
+                out = torch.empty((ndm, G), dtype=torch.int32, device="cuda")
+            for _ in range(2):
+                plan.execute(d_in, nb, G, out)
+            torch.cuda.synchronize()
+            if plan.device_status() != 0:
+                raise RuntimeError("device-side bound flag set in the format sweep")
+            plan.reset_kernel_timing()
+            plan.set_kernel_timing(True)
+            reps = 5
+            for _ in range(reps):
+                plan.execute(d_in, nb, G, out)
+            torch.cuda.synchronize()
+            plan.set_kernel_timing(False)
+            k_ms, k_n = plan.kernel_timing(1)
+            ct_ms, ct_n = plan.kernel_timing(0)
+            k_ms /= max(k_n, 1)
+            units = float(c["nchans"]) * ndm * G
+            rows_out.append({"nbits": nb, "gulp": G, "ndm": ndm,
+                             "dedisp_ms": k_ms, "corner_turn_ms": ct_ms / max(ct_n, 1),
+                             "value": units / (k_ms / 1e3) / 1e9,
+                             "frac_of_int_add_probe": units / (k_ms / 1e3) / peak})
+            del d_in, out
+            torch.cuda.empty_cache()
+    return {"workload": "format sweep: 1024 ch, trials 0-2000 (1434), 1/4/8-bit and float "
+                        "input, 2^17 and 2^20 samples; device-drawn inputs",
+            "unit": UNIT + " (dedispersion kernel)", "rows": rows_out}
+
+
 def run_graph(a):
     """Steady-state streaming of the 13 serving beams at 2^14 samples per
     gulp (device buffers): per gulp, host time to submit the work (median,
@@ -735,6 +792,8 @@ def run_ours(a, rank, world, local_rank):
         line["subband"] = run_subband(a, x, plan, out, G)
         line["subband"]["speedup_vs_direct_kernels"] = (
             k_ms / line["subband"]["early_edge"]["kernels_ms"])
+    if rank == 0 and world == 1 and not a.no_sweep and default:
+        line["format_sweep"] = run_format_sweep(a)
     if rank == 0 and world == 1 and not a.no_serving and default:
         del d_in, out
         torch.cuda.empty_cache()
