@@ -353,8 +353,9 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
     const int64_t li = item - S.item_begin;
     const int n_dmblk = S.n_dmblk;
     const int64_t per_tile = (int64_t)S.n_groups * n_dmblk;
-    const int64_t tile = li / per_tile;
-    const int64_t rem = li - tile * per_tile;
+    const int64_t lt = li / per_tile;
+    const int64_t tile = S.tile0 + lt;
+    const int64_t rem = li - lt * per_tile;
     const int grp = (int)(rem / n_dmblk);
     const int blk = (int)(rem - (int64_t)grp * n_dmblk);
     const int ndm_g = (grp == S.n_groups - 1) ? S.ndm_last : S.ndm;

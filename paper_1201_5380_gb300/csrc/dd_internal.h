@@ -69,6 +69,8 @@ struct Seg {
   int64_t out_stride;     // output row pitch (elements, or words for OUT_HALFIMG)
   int64_t nsamps;         // outputs per trial
   int64_t item_begin;     // first global item index of this segment
+  int64_t tile0;          // time tile of the segment's first item (items cover
+                          // tiles tile0 .. tile0 + n_items / per-tile items)
   int64_t g_img;          // per-group image offset, words
   int64_t g_out;          // per-group output offset, elements (words)
   int32_t g_delay;        // per-group delay-table offset, elements

@@ -125,11 +125,12 @@ def test_host_pointer_path(orc):
 
 
 def test_host_pointer_path_in_parts_with_padded_rows(orc):
-    """The host-output path runs the trial blocks in several launches and
-    copies each part out while the next computes: every row, padded stride."""
+    """The host-output path runs the time tiles in several launches and copies
+    each part's columns out while the next computes: every row and column,
+    ragged last tile, padded stride."""
     torch_cuda()
-    plan = _survey_plan(step=6)       # ~200 trials: several trial blocks per part
-    nsamps = 1300
+    plan = _survey_plan(step=6)       # ~200 trials, several trial blocks
+    nsamps = 9000                     # 9 tiles of 1024 samples: 7 parts
     rows = nsamps + plan.max_delay
     x = synth.uniform_packed(19, 0, rows, 1024, 2)
     out = np.full((plan.dm_count, nsamps + 37), 0xDEADBEEF, np.uint32)
