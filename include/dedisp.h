@@ -163,8 +163,10 @@ dd_status dd_plan_get_scrunch_factors(dd_plan plan, int32_t *factors);
 dd_status dd_plan_get_input_rows(dd_plan plan, int64_t nsamps_out, unsigned flags,
                                  int64_t *rows);
 
-/* Kernel tiling: trials per thread block (16, 32 or 64), channels staged
- * per pass (4, 8, 16 or 32) and output words per lane (2, 4 or 8; compiled
+/* Kernel tiling: trials per thread block (16, 32 or 64), the most channels
+ * staged per pass (4, 8, 16 or 32; default 32: each trial block stages as
+ * many as its windows leave room for in shared memory) and output words per
+ * lane (2, 4 or 8; compiled
  * shapes: 32x4, 64x2, 16x4, 32x2, 32x8 trials x words).  0 keeps the current
  * value.  words_per_lane < 0 (the default) picks it per input format: 8 for
  * 8-bit and float input (16- and 32-bit lanes), 4 for 1/2/4-bit input.

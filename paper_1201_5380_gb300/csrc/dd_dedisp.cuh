@@ -285,9 +285,11 @@ __device__ __forceinline__ int64_t window_word(int64_t t0, int32_t s0, int lo_sl
 //                                  window inside copies (lane 0, word 0)
 //
 // The staging tables are built on the host per plan and geometry (they do
-// not depend on the time tile): per (trial block, channel) the window start
-// and the words its trials read, and per (trial block, chunk) the B x cc
-// window offsets, which arrive by TMA with the chunk's windows.
+// not depend on the time tile): per trial block its chunk size cc and window
+// width nww (the layout above, so each block stages as many channels per
+// chunk as its own windows allow), per (trial block, channel) the window
+// start and the words its trials read, and per (trial block, chunk) the
+// B x cc window offsets, which arrive by TMA with the chunk's windows.
 //
 // Per chunk (cc channels) of an item, one __syncthreads:
 //   prefetch the next chunk's window records -> registers
@@ -295,7 +297,9 @@ __device__ __forceinline__ int64_t window_word(int64_t t0, int32_t s0, int lo_sl
 //   __syncthreads
 //   warp 0 issues the next chunk's TMA (windows + offsets)
 //   shift-and-sum this chunk
-template <int FMT, int OUTK, bool WIDE, int NWARP, int DPW, int K>
+// PBG: each trial block has its own chunk geometry (read from its staging
+// tables); otherwise the launch's (every block of the launch has the same).
+template <int FMT, int OUTK, bool WIDE, int NWARP, int DPW, int K, bool PBG>
 __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(const LaunchParams p) {
   constexpr int SPW = FmtT<FMT>::SPW;
   constexpr int LW = FmtT<FMT>::LW;
@@ -305,27 +309,40 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
 
   extern __shared__ uint4 smem4[];
   uint32_t* const sm = reinterpret_cast<uint32_t*>(smem4);
-  const int cc = p.cc;              // power of two, 4..32
-  const int cc_log = 31 - __clz(cc);
-  const int nww = p.nww;
-  const int nwl = nww + 4;
   const uint32_t sm_base = smem_addr(sm);
   const uint32_t bar0 = sm_base;    // two 8-byte mbarriers at word 0 and 2
   // one sample per word needs no shifted copies: lanes read the landing area
   constexpr bool COPIES = SPW > 1;
   uint32_t* const landing = sm + 4;
-  uint32_t* const copies = landing + 2 * cc * nwl;
-  const int landing_words = cc * nwl;
-  const int copy_words = COPIES ? cc * SPW * nww : 0;
-  uint32_t* const s_addr = copies + 2 * copy_words;
-  const int n_entries = B << cc_log;  // offsets per chunk
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
-  // the builder threads of a channel: NT / cc of them
-  const int tpc_log = (31 - __clz(NT)) - cc_log;
-  const int bc = tid >> tpc_log;
+
+  // Chunk geometry and the staging layout it implies: the launch's, set up
+  // once here, or (PBG) each trial block's, set up per work item.
+  struct Geo {
+    int cc, cc_log, nww, nwl, landing_words, copy_words, n_entries, tpc_log, bc;
+    uint32_t* copies;
+    uint32_t* s_addr;
+  };
+  auto make_geo = [&](int cc, int nww) {
+    Geo g;
+    g.cc = cc;  // power of two, 4..32
+    g.cc_log = 31 - __clz(cc);
+    g.nww = nww;  // window words (multiple of 4)
+    g.nwl = nww + 4;
+    g.copies = landing + 2 * cc * g.nwl;
+    g.landing_words = cc * g.nwl;
+    g.copy_words = COPIES ? cc * SPW * nww : 0;
+    g.s_addr = g.copies + 2 * g.copy_words;
+    g.n_entries = B << g.cc_log;  // offsets per chunk
+    // the builder threads of a channel: NT / cc of them
+    g.tpc_log = (31 - __clz(NT)) - g.cc_log;
+    g.bc = tid >> g.tpc_log;
+    return g;
+  };
+  const Geo geo_launch = make_geo(PBG ? 4 : p.cc, PBG ? 0 : p.nww);
 
   if (tid == 0) {
     mbar_init(bar0, 1);
@@ -359,6 +376,15 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
     const int grp = (int)(rem / n_dmblk);
     const int blk = (int)(rem - (int64_t)grp * n_dmblk);
     const int ndm_g = (grp == S.n_groups - 1) ? S.ndm_last : S.ndm;
+    // this item's staging tables: the trial block's chunk geometry, then one
+    // window record per channel (a per-block geometry load is issued here,
+    // beside the block-start loads, rather than after them)
+    const int nchan = S.nchan;
+    const int2* __restrict__ crec_g =
+        reinterpret_cast<const int2*>(S.crec + (int64_t)grp * S.g_crec);
+    const int2* __restrict__ crec = crec_g + (int64_t)blk * nchan;
+    int2 bgeo = make_int2(0, 0);
+    if constexpr (PBG) bgeo = __ldg(&crec_g[(int64_t)n_dmblk * nchan + blk]);
     int d0, nd;
     if (S.blk) {
       const int32_t* bt = S.blk + (int64_t)grp * (n_dmblk + 1);
@@ -371,7 +397,6 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
     }
     const int64_t t0 = tile * T;
     const int64_t t_end = min(t0 + T, S.nsamps);
-    const int nchan = S.nchan;
     const int64_t row_words = S.row_words;
     const uint32_t* __restrict__ img = S.img + (int64_t)grp * S.g_img;
     uint32_t* const out_g = reinterpret_cast<uint32_t*>(S.out) + (int64_t)grp * S.g_out;
@@ -379,12 +404,15 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       if (tid == 0) atomicOr(p.status, DEV_BAD_ITEM);
       continue;
     }
+    const Geo G = PBG ? make_geo(bgeo.x, bgeo.y) : geo_launch;
+    const int cc = G.cc, cc_log = G.cc_log, nww = G.nww, nwl = G.nwl;
+    uint32_t* const copies = G.copies;
+    uint32_t* const s_addr = G.s_addr;
+    const int landing_words = G.landing_words, copy_words = G.copy_words;
+    const int n_entries = G.n_entries, tpc_log = G.tpc_log, bc = G.bc;
     const int nchunks = (nchan + cc - 1) >> cc_log;
-    // this item's staging tables
-    const int2* __restrict__ crec = reinterpret_cast<const int2*>(
-        S.crec + (int64_t)grp * S.g_crec + (int64_t)blk * nchan * 2);
     const uint32_t* __restrict__ atab =
-        S.atab + (int64_t)grp * S.g_atab + (int64_t)blk * nchunks * n_entries;
+        S.atab + (int64_t)grp * S.g_atab + (int64_t)blk * S.atab_blk;
     const int64_t t0w = t0 / SPW;  // image word of time t0 - kPad
 
     // window record of channel c0 + (warp 0: lane; builders: bc) of chunk k
@@ -659,9 +687,9 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
 }
 
 // Host helpers used by the per-format translation units.
-template <int FMT, int OUTK, bool WIDE, int NWARP, int DPW, int K>
+template <int FMT, int OUTK, bool WIDE, int NWARP, int DPW, int K, bool PBG>
 cudaError_t launch_one(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
-  auto kern = k_dedisp<FMT, OUTK, WIDE, NWARP, DPW, K>;
+  auto kern = k_dedisp<FMT, OUTK, WIDE, NWARP, DPW, K, PBG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -669,26 +697,33 @@ cudaError_t launch_one(const LaunchParams& p, int grid, size_t smem, cudaStream_
   return cudaGetLastError();
 }
 
-template <int FMT, int OUTK, bool WIDE, int NWARP, int DPW, int K>
+template <int FMT, int OUTK, bool WIDE, int NWARP, int DPW, int K, bool PBG>
 cudaError_t occupancy_one(size_t smem, int* nblk) {
-  auto kern = k_dedisp<FMT, OUTK, WIDE, NWARP, DPW, K>;
+  auto kern = k_dedisp<FMT, OUTK, WIDE, NWARP, DPW, K, PBG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nblk, kern, NWARP * 32, smem);
 }
 
-// Dispatch over the compiled tile shapes for one (FMT, OUTK, WIDE).
+template <int FMT, int OUTK, bool WIDE, int NWARP, int DPW, int K, bool PBG>
+cudaError_t run_one(const LaunchParams* p, int grid, size_t smem, cudaStream_t st, int* occ) {
+  return occ ? occupancy_one<FMT, OUTK, WIDE, NWARP, DPW, K, PBG>(smem, occ)
+             : launch_one<FMT, OUTK, WIDE, NWARP, DPW, K, PBG>(*p, grid, smem, st);
+}
+
+// Dispatch over the compiled tile shapes (and the per-block geometry
+// variant) for one (FMT, OUTK, WIDE).
 template <int FMT, int OUTK, bool WIDE>
-cudaError_t dispatch_cfg(int cfg, const LaunchParams* p, int grid, size_t smem,
+cudaError_t dispatch_cfg(int cfg, bool pbg, const LaunchParams* p, int grid, size_t smem,
                          cudaStream_t st, int* occ) {
   switch (cfg) {
 #define DD_CFG_CASE(I)                                                                   \
   case I:                                                                                \
-    return occ ? occupancy_one<FMT, OUTK, WIDE, kTileCfgs[I].nwarp, kTileCfgs[I].dpw,     \
-                               kTileCfgs[I].k>(smem, occ)                                \
-               : launch_one<FMT, OUTK, WIDE, kTileCfgs[I].nwarp, kTileCfgs[I].dpw,        \
-                            kTileCfgs[I].k>(*p, grid, smem, st);
+    return pbg ? run_one<FMT, OUTK, WIDE, kTileCfgs[I].nwarp, kTileCfgs[I].dpw,          \
+                         kTileCfgs[I].k, true>(p, grid, smem, st, occ)                   \
+               : run_one<FMT, OUTK, WIDE, kTileCfgs[I].nwarp, kTileCfgs[I].dpw,          \
+                         kTileCfgs[I].k, false>(p, grid, smem, st, occ);
     DD_CFG_CASE(0)
     DD_CFG_CASE(1)
     DD_CFG_CASE(2)

@@ -149,46 +149,112 @@ struct SegSpec {
 // woff = floor((kPad + s0 - lo) / (4 SPW)) * 4 with s0 the block's first
 // delay; trial slot i (slots past the block's last trial repeat it) reads
 // lane-shifted copy kap = o mod SPW from word o / SPW, o = kPad + s_i -
-// woff*SPW.  Absent channels of a last partial chunk read the zero window.
-static dd_status build_stage_tab(const TabSrc& src, int spw, int B, int K, int cc, int nww,
-                                 StageTab* t) {
-  const int nchunks = (src.nchan + cc - 1) / cc;
+// woff*SPW.  Each block gets its own chunk geometry: its window width nww
+// is the widest read span of its channels, and its chunk the most channels
+// (up to cc_cap) whose two staging buffers fit in shared memory, so blocks
+// with a small delay spread stage more channels per barrier than the
+// launch's widest block could.  When every block gets the same chunk, all
+// of them take the window width nww_uniform instead (at least the widest
+// span): one geometry for the launch, which the kernel then reads from its
+// parameters rather than per block.  Absent channels of a last partial
+// chunk read the zero window.
+static dd_status build_stage_tab(const TabSrc& src, int fmt, int cfg, int cc_cap,
+                                 int nww_uniform, StageTab* t) {
+  const int spw = fmt_spw(fmt);
+  const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
+  const int K = kTileCfgs[cfg].k;
+  const int nt = kTileCfgs[cfg].nwarp * 32;
   const bool copies = spw > 1;
-  const int nwl = nww + 4;
-  const int64_t per_blk = (int64_t)nchunks * B * cc;
-  t->g_atab = (int64_t)src.nblk * per_blk;
-  t->g_crec = (int64_t)src.nblk * src.nchan * 2;
+  t->atab_blk = (int64_t)((src.nchan + cc_cap - 1) / cc_cap) * cc_cap * B;
+  t->g_atab = (int64_t)src.nblk * t->atab_blk;
+  t->g_crec = (int64_t)src.nblk * (src.nchan + 1) * 2;
   t->atab.assign((size_t)(t->g_atab * src.ngroups), 0u);
   t->crec.assign((size_t)(t->g_crec * src.ngroups), 0);
+  t->smem = 0;
+  // window start of (block, channel) and the words its trials read
+  auto window = [&](const int32_t* dl, int d0, int d1, int c, int64_t* woff,
+                    int64_t* span) -> bool {
+    const int64_t b0 = (int64_t)kPad + dl[(int64_t)d0 * src.dstride + c] - src.lo;
+    if (b0 < 0) return false;
+    *woff = b0 / (4 * spw) * 4;
+    int64_t sp = 0;
+    for (int i = 0; i < B; ++i) {
+      const int d = std::min(d0 + i, d1 - 1);
+      const int64_t o = (int64_t)kPad + dl[(int64_t)d * src.dstride + c] - *woff * spw;
+      if (o < 0) return false;
+      sp = std::max<int64_t>(sp, o / spw + 32 * K);
+    }
+    *span = sp;
+    return true;
+  };
+  auto fits = [&](int cc, int nww) {
+    return dedisp_smem_bytes(fmt, cfg, cc, nww) <= kSmemCap && B * cc <= 2 * nt;
+  };
+  // pass 1: each block's widest span and the chunk it allows
+  std::vector<int> bcc((size_t)src.ngroups * src.nblk, 0), bnww(bcc.size(), 0);
+  int cc_lo = INT_MAX, cc_hi = 0, nww_hi = 0;
   for (int g = 0; g < src.ngroups; ++g) {
     const int32_t* dl = src.delays + (int64_t)g * src.g_delay;
     const int32_t* bt = src.blk + (int64_t)g * (src.nblk + 1);
     for (int b = 0; b < src.nblk; ++b) {
       const int d0 = bt[b], d1 = bt[b + 1];
       if (d1 <= d0) continue;  // padding block: never visited
-      uint32_t* at = t->atab.data() + g * t->g_atab + b * per_blk;
-      int32_t* cr = t->crec.data() + g * t->g_crec + (int64_t)b * src.nchan * 2;
+      int64_t widest = 0, woff, span;
+      for (int c = 0; c < src.nchan; ++c) {
+        if (!window(dl, d0, d1, c, &woff, &span)) return DD_ERR_INVALID_ARG;
+        widest = std::max(widest, span);
+      }
+      if (widest > INT_MAX / 64) return DD_ERR_INVALID_ARG;
+      const int nww = (int)((widest + 3) & ~3);
+      int cc = cc_cap;
+      while (cc > 4 && !fits(cc, nww)) cc /= 2;
+      if (!fits(cc, nww)) return DD_ERR_INVALID_ARG;
+      bcc[(size_t)g * src.nblk + b] = cc;
+      bnww[(size_t)g * src.nblk + b] = nww;
+      cc_lo = std::min(cc_lo, cc);
+      cc_hi = std::max(cc_hi, cc);
+      nww_hi = std::max(nww_hi, nww);
+    }
+  }
+  t->uniform = cc_hi > 0 && cc_lo == cc_hi;
+  if (t->uniform) {
+    t->cc = cc_hi;
+    t->nww = std::max(nww_hi, (nww_uniform + 3) & ~3);
+    if (!fits(t->cc, t->nww)) t->nww = nww_hi;
+  }
+  // pass 2: the tables
+  for (int g = 0; g < src.ngroups; ++g) {
+    const int32_t* dl = src.delays + (int64_t)g * src.g_delay;
+    const int32_t* bt = src.blk + (int64_t)g * (src.nblk + 1);
+    for (int b = 0; b < src.nblk; ++b) {
+      const int d0 = bt[b], d1 = bt[b + 1];
+      if (d1 <= d0) continue;
+      const int cc = t->uniform ? t->cc : bcc[(size_t)g * src.nblk + b];
+      const int nww = t->uniform ? t->nww : bnww[(size_t)g * src.nblk + b];
+      t->smem = std::max(t->smem, dedisp_smem_bytes(fmt, cfg, cc, nww));
+      int32_t* cg = t->crec.data() + g * t->g_crec;
+      cg[((int64_t)src.nblk * src.nchan + b) * 2] = cc;
+      cg[((int64_t)src.nblk * src.nchan + b) * 2 + 1] = nww;
+      int32_t* cr = cg + (int64_t)b * src.nchan * 2;
+      uint32_t* at = t->atab.data() + g * t->g_atab + b * t->atab_blk;
+      const int nchunks = (src.nchan + cc - 1) / cc;
       for (int c = 0; c < nchunks * cc; ++c) {
         const int cl = c % cc;
         uint32_t* a = at + (int64_t)(c / cc) * B * cc + cl;
         if (c >= src.nchan) {
-          const uint32_t zero = (uint32_t)(copies ? cl * spw * nww : cl * nwl) * 4u;
+          const uint32_t zero = (uint32_t)(copies ? cl * spw * nww : cl * (nww + 4)) * 4u;
           for (int i = 0; i < B; ++i) a[(int64_t)i * cc] = zero;
           continue;
         }
-        const int64_t b0 = (int64_t)kPad + dl[(int64_t)d0 * src.dstride + c] - src.lo;
-        if (b0 < 0) return DD_ERR_INVALID_ARG;
-        const int64_t woff = b0 / (4 * spw) * 4;
-        int64_t span = 0;
+        int64_t woff, span;
+        window(dl, d0, d1, c, &woff, &span);
         for (int i = 0; i < B; ++i) {
           const int d = std::min(d0 + i, d1 - 1);
           const int64_t o = (int64_t)kPad + dl[(int64_t)d * src.dstride + c] - woff * spw;
           const int64_t om = o / spw;
-          if (o < 0 || om + 32 * K > nww) return DD_ERR_INVALID_ARG;
           const int64_t kap = o & (spw - 1);
-          span = std::max<int64_t>(span, om + 32 * K);
-          a[(int64_t)i * cc] =
-              (uint32_t)(copies ? ((cl * spw + kap) * nww + om) * 4 : (cl * nwl + om) * 4);
+          a[(int64_t)i * cc] = (uint32_t)(copies ? ((cl * spw + kap) * nww + om) * 4
+                                                 : (cl * (nww + 4) + om) * 4);
         }
         cr[2 * c] = (int32_t)woff;
         cr[2 * c + 1] = (int32_t)span;
@@ -198,14 +264,14 @@ static dd_status build_stage_tab(const TabSrc& src, int spw, int B, int K, int c
   return DD_OK;
 }
 
-StageTab* stage_tab(Plan& p, int kind, const TabSrc& src, int spw, int B, int K, int cc,
-                    int nww, bool upload, dd_status* err) {
-  const std::array<int, 7> key = {kind, B, spw, K, cc, nww, src.lo};
+StageTab* stage_tab(Plan& p, int kind, const TabSrc& src, int fmt, int cfg, int cc_cap,
+                    int nww_uniform, bool upload, dd_status* err) {
+  const std::array<int, 7> key = {kind, cfg, fmt, cc_cap, src.lo, nww_uniform, src.nblk};
   auto it = p.tabs.find(key);
   if (it == p.tabs.end()) {
     if (p.tabs.size() >= 16) p.tabs.clear();  // bounded cache (frees synchronise the device)
     std::unique_ptr<StageTab> t(new StageTab);
-    *err = build_stage_tab(src, spw, B, K, cc, nww, t.get());
+    *err = build_stage_tab(src, fmt, cfg, cc_cap, nww_uniform, t.get());
     if (*err != DD_OK) return nullptr;
     it = p.tabs.emplace(key, std::move(t)).first;
   }
@@ -255,9 +321,8 @@ int chunk_channels(const Plan& p, int fmt, int32_t spread) {
   const int nt = kTileCfgs[cfg].nwarp * 32;
   int cc = 4;
   while (cc * 2 <= p.tune.chans_per_chunk) cc *= 2;
-  const size_t smem_cap = 220 * 1024;
-  while (cc > 4 && (dedisp_smem_bytes(fmt, cfg, cc, nww) > smem_cap || B * cc > 2 * nt)) cc /= 2;
-  if (dedisp_smem_bytes(fmt, cfg, cc, nww) > smem_cap || B * cc > 2 * nt) return 0;
+  while (cc > 4 && (dedisp_smem_bytes(fmt, cfg, cc, nww) > kSmemCap || B * cc > 2 * nt)) cc /= 2;
+  if (dedisp_smem_bytes(fmt, cfg, cc, nww) > kSmemCap || B * cc > 2 * nt) return 0;
   return cc;
 }
 
@@ -267,15 +332,11 @@ static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector
   const int cfg = tile_cfg_index(tuning_for(p.tune, fmt));
   const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
   const int T = time_tile(fmt, tuning_for(p.tune, fmt));
-  int32_t spread = 0;
   int nchan_max = 0;
-  for (auto& s : specs) {
-    spread = std::max(spread, s.spread);
-    nchan_max = std::max(nchan_max, (int)s.seg.nchan);
-  }
-  const int nww = window_words(fmt, tuning_for(p.tune, fmt), spread);
-  const int cc = chunk_channels(p, fmt, spread);
-  if (cc == 0) return DD_ERR_INVALID_ARG;
+  for (auto& s : specs) nchan_max = std::max(nchan_max, (int)s.seg.nchan);
+  // largest channels per chunk (the staging tables pick each block's own)
+  int cc_cap = 4;
+  while (cc_cap * 2 <= p.tune.chans_per_chunk) cc_cap *= 2;
 
   L->fmt = fmt;
   L->outk = outk;
@@ -304,8 +365,6 @@ static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector
   std::memset(&lp, 0, sizeof(lp));
   lp.n_segs = (int32_t)L->segs.size();
   for (size_t i = 0; i < L->segs.size(); ++i) lp.segs[i] = L->segs[i];
-  lp.nww = nww;
-  lp.cc = cc;
   lp.f0 = f0;
   lp.f1 = f1;
   lp.f2 = f2;
@@ -323,28 +382,47 @@ static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector
     lp.out_shift = std::max(0, bl - p.out_bits);
     L->outk = OUT_NARROW;
   }
-  // staging tables of each segment for this geometry
+  // staging tables of each segment; shared memory for the widest block.  If
+  // every block of every segment has one geometry, the kernel takes it from
+  // the launch parameters.
+  size_t smem = 0;
+  bool uniform = true;
+  int ucc = 0, unww = 0;
   {
     size_t i = 0;
     for (auto& sp : specs) {
       if (sp.seg.ndm <= 0 || sp.seg.nsamps <= 0) continue;
       dd_status err;
-      StageTab* t = stage_tab(*sp.owner, sp.kind, sp.src, fmt_spw(fmt), B,
-                              kTileCfgs[cfg].k, cc, nww, !sp.no_upload, &err);
+      StageTab* t = stage_tab(*sp.owner, sp.kind, sp.src, fmt, cfg, cc_cap,
+                              window_words(fmt, tuning_for(p.tune, fmt), sp.spread),
+                              !sp.no_upload, &err);
       if (!t) return err;
+      // the kernel finds a block's geometry after the group's nblk x nchan
+      // window records
+      if (lp.segs[i].n_dmblk != sp.src.nblk || lp.segs[i].nchan != sp.src.nchan)
+        return DD_ERR_INVALID_ARG;
+      if (!t->uniform || (ucc && (t->cc != ucc || t->nww != unww))) uniform = false;
+      ucc = t->cc;
+      unww = t->nww;
       sp.tab = t;
       Seg& g = lp.segs[i];
       g.atab = sp.no_upload ? nullptr : static_cast<const uint32_t*>(t->d_atab.p);
       g.crec = sp.no_upload ? nullptr : static_cast<const int32_t*>(t->d_crec.p);
       g.g_atab = t->g_atab;
       g.g_crec = t->g_crec;
+      g.atab_blk = t->atab_blk;
       L->segs[i] = g;
+      smem = std::max(smem, t->smem);
       ++i;
     }
   }
-  L->smem = dedisp_smem_bytes(fmt, cfg, cc, nww);
+  L->smem = smem;
+  lp.per_block_geo = uniform ? 0 : 1;
+  lp.cc = uniform ? ucc : 0;
+  lp.nww = uniform ? unww : 0;
   int per_sm = 0;
-  cudaError_t e = dedisp_max_blocks_per_sm(fmt, L->outk, wide, cfg, L->smem, &per_sm);
+  cudaError_t e = dedisp_max_blocks_per_sm(fmt, L->outk, wide, cfg, lp.per_block_geo != 0,
+                                           L->smem, &per_sm);
   if (e != cudaSuccess) return cuda_status(e);
   if (per_sm < 1) return DD_ERR_INVALID_ARG;
   const int64_t resident = (int64_t)per_sm * std::max(1, p.num_sms);

@@ -82,12 +82,16 @@ struct Seg {
   int32_t nchan;          // channels summed
   int32_t lo_slack;       // max_{block,c} delay(d0,c) - min_{d in block} delay(d,c)
   // Staging tables of the launch geometry (built on the host, see StageTab):
-  const uint32_t* atab;   // [group][block][chunk][trial slot][channel of chunk]
-                          // byte offset of the (trial, channel) window
-  const int32_t* crec;    // [group][block][channel] {window start word - t0/SPW,
-                          // words of the window the block's trials read}
+  const uint32_t* atab;   // [group][block: atab_blk][chunk][trial slot][channel
+                          // of chunk] byte offset of the (trial, channel) window
+  const int32_t* crec;    // per group, pairs: [block][channel] {window start word
+                          // - t0/SPW, words of the window the block's trials
+                          // read}, then [block] the block's chunk geometry
+                          // {channels per chunk, window words}
   int64_t g_atab;         // per-group offsets of the two tables (elements)
   int64_t g_crec;
+  int64_t atab_blk;       // atab entries per block (channels rounded up to the
+                          // largest chunk, x trial slots)
 };
 
 constexpr int kMaxSegs = 32;  // segments per launch, passed inline as a kernel parameter
@@ -95,8 +99,10 @@ constexpr int kMaxSegs = 32;  // segments per launch, passed inline as a kernel 
 struct LaunchParams {
   Seg segs[kMaxSegs];
   int32_t n_segs;
-  int32_t nww;       // words per staged copy window (multiple of 4)
-  int32_t cc;        // channels per staged chunk (multiple of 4)
+  // chunk geometry: per trial block from its staging tables (per_block_geo),
+  // else every block of the launch stages cc channels in windows of nww words
+  int32_t per_block_geo;
+  int32_t cc, nww;
   int32_t f0, f1, f2;  // flush periods (groups of 4 channels) per level
   int64_t n_items;
   uint32_t* status;
@@ -130,7 +136,7 @@ constexpr int kNumTileCfgs = 5;
 // Host launchers (dd_kernels_*.cu).
 cudaError_t launch_dedisp(int fmt, int outk, bool wide, int cfg, const LaunchParams& p,
                           int grid, size_t smem, cudaStream_t st);
-cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, size_t smem,
+cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, bool pbg, size_t smem,
                                      int* nblk);
 cudaError_t launch_corner_turn(int nbits, const uint8_t* in, int64_t in_stride,
                                int64_t t_begin, int64_t nrows_valid, int nchans,
@@ -154,7 +160,7 @@ struct DevBuf {
 
 struct Tuning {
   int dms_per_block = 32;
-  int chans_per_chunk = 8;
+  int chans_per_chunk = 32;  // the most; each trial block's own fits its windows
   int words_per_lane = 0;  // 0: chosen per input format (tuning_for)
 };
 
@@ -166,7 +172,10 @@ struct StageTab {
   bool uploaded = false;
   std::vector<uint32_t> atab;  // see Seg::atab
   std::vector<int32_t> crec;   // see Seg::crec (pairs)
-  int64_t g_atab = 0, g_crec = 0;
+  int64_t g_atab = 0, g_crec = 0, atab_blk = 0;
+  size_t smem = 0;             // dynamic shared memory of the widest block
+  bool uniform = false;        // every block has chunk geometry (cc, nww)
+  int cc = 0, nww = 0;
   DevBuf d_atab, d_crec;
 };
 
@@ -334,6 +343,8 @@ void make_blocks(const int32_t* delays, int ndm, int nchans, int stride, int B,
 // staging and 4-channel chunks the windows of every format then fit in
 // 220 KB of shared memory.
 constexpr int32_t kSpreadBudget = 4000;
+// Dynamic shared memory a dedispersion block may use for its staging buffers.
+constexpr size_t kSmemCap = 220 * 1024;
 int time_tile(int fmt, const Tuning& t);
 int out_elem_bytes(const Plan& p, int outk);
 bool out_vec_ok(const void* out, int64_t stride_elems, int esz);
@@ -347,8 +358,8 @@ dd_status run_launch(Plan& p, LaunchPlan& lpl, cudaStream_t st);
 // The plan's staging tables of `src` (kind 0 direct, 1/2 sub-band stage)
 // for a launch geometry, built on first use and uploaded when asked; null
 // with *err set if a window would not fit the geometry.
-StageTab* stage_tab(Plan& p, int kind, const TabSrc& src, int spw, int B, int K, int cc,
-                    int nww, bool upload, dd_status* err);
+StageTab* stage_tab(Plan& p, int kind, const TabSrc& src, int fmt, int cfg, int cc_cap,
+                    int nww_uniform, bool upload, dd_status* err);
 void drop_stage_tabs(Plan& p, int kind_mask);
 dd_status stage_direct_image(Plan& p, const void* in, int nbits, int64_t in_stride, int64_t rows,
                              int64_t nsamps, DevBuf& image, cudaStream_t st, DirectJob* j);

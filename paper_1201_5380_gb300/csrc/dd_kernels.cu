@@ -7,31 +7,35 @@
 
 namespace dd {
 
-cudaError_t dispatch_nib(int, bool, int, const LaunchParams*, int, size_t, cudaStream_t, int*);
-cudaError_t dispatch_byte(int, bool, int, const LaunchParams*, int, size_t, cudaStream_t, int*);
-cudaError_t dispatch_half(int, bool, int, const LaunchParams*, int, size_t, cudaStream_t, int*);
-cudaError_t dispatch_word(int, int, bool, int, const LaunchParams*, int, size_t, cudaStream_t,
+cudaError_t dispatch_nib(int, bool, int, bool, const LaunchParams*, int, size_t, cudaStream_t,
+                         int*);
+cudaError_t dispatch_byte(int, bool, int, bool, const LaunchParams*, int, size_t, cudaStream_t,
                           int*);
+cudaError_t dispatch_half(int, bool, int, bool, const LaunchParams*, int, size_t, cudaStream_t,
+                          int*);
+cudaError_t dispatch_word(int, int, bool, int, bool, const LaunchParams*, int, size_t,
+                          cudaStream_t, int*);
 
-static cudaError_t dispatch(int fmt, int outk, bool wide, int cfg, const LaunchParams* p,
-                            int grid, size_t smem, cudaStream_t st, int* occ) {
+static cudaError_t dispatch(int fmt, int outk, bool wide, int cfg, bool pbg,
+                            const LaunchParams* p, int grid, size_t smem, cudaStream_t st,
+                            int* occ) {
   switch (fmt) {
-    case FMT_NIB: return dispatch_nib(outk, wide, cfg, p, grid, smem, st, occ);
-    case FMT_BYTE: return dispatch_byte(outk, wide, cfg, p, grid, smem, st, occ);
-    case FMT_HALF: return dispatch_half(outk, wide, cfg, p, grid, smem, st, occ);
-    default: return dispatch_word(fmt, outk, wide, cfg, p, grid, smem, st, occ);
+    case FMT_NIB: return dispatch_nib(outk, wide, cfg, pbg, p, grid, smem, st, occ);
+    case FMT_BYTE: return dispatch_byte(outk, wide, cfg, pbg, p, grid, smem, st, occ);
+    case FMT_HALF: return dispatch_half(outk, wide, cfg, pbg, p, grid, smem, st, occ);
+    default: return dispatch_word(fmt, outk, wide, cfg, pbg, p, grid, smem, st, occ);
   }
 }
 
 cudaError_t launch_dedisp(int fmt, int outk, bool wide, int cfg, const LaunchParams& p,
                           int grid, size_t smem, cudaStream_t st) {
-  return dispatch(fmt, outk, wide, cfg, &p, grid, smem, st, nullptr);
+  return dispatch(fmt, outk, wide, cfg, p.per_block_geo != 0, &p, grid, smem, st, nullptr);
 }
 
-cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, size_t smem,
+cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, bool pbg, size_t smem,
                                      int* nblk) {
   *nblk = 0;
-  return dispatch(fmt, outk, wide, cfg, nullptr, 0, smem, nullptr, nblk);
+  return dispatch(fmt, outk, wide, cfg, pbg, nullptr, 0, smem, nullptr, nblk);
 }
 
 // Two mbarriers, then two buffers each of: landing windows (cc x (nww+4)),

@@ -455,7 +455,7 @@ dd_status dd_plan_autotune(dd_plan plan, int nbits, int64_t nsamps, void* cuda_s
   const Tuning saved = p->tune;
   Tuning best = saved;
   float best_ms = 1e30f;
-  static const int ccs[] = {4, 8, 16};
+  static const int ccs[] = {8, 16, 32};
   dd_status result = DD_OK;
   for (int ci = 0; ci < kNumTileCfgs && result == DD_OK; ++ci) {
     for (int cc : ccs) {

@@ -140,7 +140,8 @@ def test_host_pointer_path_in_parts_with_padded_rows(orc):
     assert np.all(out[:, nsamps:] == 0xDEADBEEF)
 
 
-@pytest.mark.parametrize("tiling", [(32, 4, 4), (32, 8, 4), (32, 16, 4), (64, 8, 2), (64, 4, 2),
+@pytest.mark.parametrize("tiling", [(32, 4, 4), (32, 8, 4), (32, 16, 4), (32, 32, 4), (16, 32, 4),
+                                    (64, 8, 2), (64, 4, 2),
                                     (16, 4, 4), (16, 8, 4), (32, 4, 2), (32, 8, 2), (32, 16, 2),
                                     (32, 8, 8)])
 def test_every_tiling_bit_exact(orc, tiling):

@@ -105,7 +105,7 @@ def test_plan_validation():
 
 def test_tuning_api():
     p = dd.Plan(64, 64e-6, 1500.0, -1.0, dms=[0.0, 1.0])
-    assert p.get_tuning() == dict(dms_per_block=32, chans_per_chunk=8, words_per_lane=0)
+    assert p.get_tuning() == dict(dms_per_block=32, chans_per_chunk=32, words_per_lane=0)
     p.set_tuning(32, 8, 8)
     assert p.get_tuning()["words_per_lane"] == 8
     p.set_tuning(0, 0, -1)                         # back to per-format choice
