@@ -135,8 +135,8 @@ class ClockSampler:
 # 2^17 output samples, from ncu, per (input bits, largest trial DM), with the
 # summary that holds the capture; the traffic grows in proportion to the gulp.
 DEDISP_TRAFFIC_2E17 = {
-    (2, 1000.0): (77.082624e6 + 568.520960e6, "profiles/k_dedisp_survey_ncu_full.md"),
-    (8, 2000.0): (524.967936e6 + 732.557568e6, "profiles/k_dedisp_8bit_dm2000_ncu_full.md"),
+    (2, 1000.0): (77.189632e6 + 568.246016e6, "profiles/k_dedisp_survey_ncu_full.md"),
+    (8, 2000.0): (470.875136e6 + 732.305664e6, "profiles/k_dedisp_8bit_dm2000_ncu_full.md"),
 }
 
 
