@@ -279,7 +279,9 @@ __device__ __forceinline__ int64_t window_word(int64_t t0, int32_t s0, int lo_sl
 
 // Shared-memory layout (32-bit words), two buffers of each region:
 //   [0,4)            two mbarriers
-//   landing[2][cc][nww+4]          TMA destination: raw image windows
+//   landing[1 or 2][cc][nww+4]     TMA destination: raw image windows (one
+//                                  buffer when the shifted copies are built
+//                                  from it, two when lanes read it directly)
 //   copies [2][cc*SPW][nww]        SPW lane-shifted copies of each window
 //   addr   [2][B*cc]               byte offset of each (trial, channel)
 //                                  window inside copies (lane 0, word 0)
@@ -332,8 +334,12 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
     g.cc_log = 31 - __clz(cc);
     g.nww = nww;  // window words (multiple of 4)
     g.nwl = nww + 4;
-    g.copies = landing + 2 * cc * g.nwl;
-    g.landing_words = cc * g.nwl;
+    // with shifted copies the landing area is read only by the build, which
+    // the chunk's barrier ends before the next chunk's windows are requested:
+    // one landing buffer serves both (stride 0); without copies the sums read
+    // it, so it is double-buffered
+    g.copies = landing + (COPIES ? 1 : 2) * cc * g.nwl;
+    g.landing_words = COPIES ? 0 : cc * g.nwl;
     g.copy_words = COPIES ? cc * SPW * nww : 0;
     g.s_addr = g.copies + 2 * g.copy_words;
     g.n_entries = B << g.cc_log;  // offsets per chunk

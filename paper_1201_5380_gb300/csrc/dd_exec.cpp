@@ -311,21 +311,6 @@ bool out_vec_ok(const void* out, int64_t stride_elems, int esz) {
   return !(reinterpret_cast<uintptr_t>(out) & 15) && !((stride_elems * esz) & 15);
 }
 
-// Channels per chunk for a launch whose largest staging spread is `spread`:
-// a power of two, at most two address-table entries per thread, and both
-// staging buffers within the shared-memory budget (0 if nothing fits).
-int chunk_channels(const Plan& p, int fmt, int32_t spread) {
-  const int cfg = tile_cfg_index(tuning_for(p.tune, fmt));
-  const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
-  const int nww = window_words(fmt, tuning_for(p.tune, fmt), spread);
-  const int nt = kTileCfgs[cfg].nwarp * 32;
-  int cc = 4;
-  while (cc * 2 <= p.tune.chans_per_chunk) cc *= 2;
-  while (cc > 4 && (dedisp_smem_bytes(fmt, cfg, cc, nww) > kSmemCap || B * cc > 2 * nt)) cc /= 2;
-  if (dedisp_smem_bytes(fmt, cfg, cc, nww) > kSmemCap || B * cc > 2 * nt) return 0;
-  return cc;
-}
-
 // Fill launch parameters for a set of segments sharing one staged format.
 static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector<SegSpec>& specs,
                                bool vec_out, LaunchPlan* L) {

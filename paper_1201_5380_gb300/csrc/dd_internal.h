@@ -348,9 +348,6 @@ constexpr size_t kSmemCap = 220 * 1024;
 int time_tile(int fmt, const Tuning& t);
 int out_elem_bytes(const Plan& p, int outk);
 bool out_vec_ok(const void* out, int64_t stride_elems, int esz);
-// Channels per staged chunk that plan p's tiling gives a launch whose
-// largest staging spread is `spread` (0 if it cannot be staged).
-int chunk_channels(const Plan& p, int fmt, int32_t spread);
 dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
                              const std::vector<DirectJob>& jobs, LaunchPlan* lpl,
                              std::vector<StageTab*>* tabs = nullptr);

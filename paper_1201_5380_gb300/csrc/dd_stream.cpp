@@ -289,26 +289,20 @@ dd_status dd_batch_launch(dd_batch b, void* cuda_stream, int64_t* nsamps_out) {
     }
   }
   // The launches use the first plan's tiling; segments carry each beam's
-  // tables.  A launch stages windows as wide as its widest segment needs,
-  // and wider windows leave room for fewer channels per chunk, so beams are
-  // grouped by the chunk size they would get alone: one persistent launch
-  // per group (and per kMaxSegs beams).  Inside a launch, beams of the same
-  // shape (channels, trials) are kept adjacent in the work list: on the
-  // serving workload, interleaving 512- and 1024-channel beams made the
-  // launch 13-26 % slower than the same beams grouped.
+  // tables, and each trial block its own chunk size, so beams of any
+  // geometry share one persistent launch (per kMaxSegs beams).  Inside a
+  // launch, beams of the same shape (channels, trials) are kept adjacent in
+  // the work list: on the serving workload, interleaving 512- and
+  // 1024-channel beams made the launch 13-26 % slower than the same beams
+  // grouped.
   {
-    const int c0 = tile_cfg_index(tuning_for(p0.tune, fmt));
-    const int bi = b_index(kTileCfgs[c0].nwarp * kTileCfgs[c0].dpw);
     struct Key {
-      int cc, nchans, ndm;
+      int nchans, ndm;
       size_t job;
     };
     std::vector<Key> key;
-    for (size_t k = 0; k < jobs.size(); ++k)
-      key.push_back({chunk_channels(p0, fmt, jobs[k].plan->spread_B[bi]), jobs[k].nchans,
-                     jobs[k].ndm, k});
+    for (size_t k = 0; k < jobs.size(); ++k) key.push_back({jobs[k].nchans, jobs[k].ndm, k});
     std::stable_sort(key.begin(), key.end(), [](const Key& a, const Key& b) {
-      if (a.cc != b.cc) return a.cc > b.cc;
       if (a.nchans != b.nchans) return a.nchans < b.nchans;
       return a.ndm < b.ndm;
     });
@@ -316,7 +310,7 @@ dd_status dd_batch_launch(dd_batch b, void* cuda_stream, int64_t* nsamps_out) {
     while (k0 < key.size()) {
       size_t k1 = k0;
       std::vector<DirectJob> part;
-      while (k1 < key.size() && key[k1].cc == key[k0].cc && part.size() < (size_t)kMaxSegs)
+      while (k1 < key.size() && part.size() < (size_t)kMaxSegs)
         part.push_back(jobs[key[k1++].job]);
       LaunchPlan L;
       dd_status r = plan_direct_launch(p0, fmt, fmt == FMT_F32 ? OUT_F32 : OUT_U32,
