@@ -179,6 +179,55 @@ __global__ void __launch_bounds__(256) k_corner_turn_2bit(const uint8_t* __restr
   }
 }
 
+// 8-bit input, 16-byte-aligned rows: the serving bands, specialised.  Block
+// = 256 threads over 64 channels (64 input bytes per row) x 64 image words
+// (128 rows).  Phase 1: each thread loads 16-byte pieces of rows and stores
+// their bytes transposed (channel major), so 8 consecutive samples of one
+// channel are 8 consecutive bytes.  Phase 2: a thread reads 8 samples of a
+// channel with one 64-bit load and writes the 4 image words they make (two
+// 16-bit lanes each) with one 16-byte store.  Requires in, in_stride 16-byte
+// aligned, nchans % 64 == 0, row_words and words multiples of 4.
+__global__ void __launch_bounds__(256) k_corner_turn_8bit(const uint8_t* __restrict__ in,
+                                                          int64_t in_stride, int64_t t_begin,
+                                                          int64_t nrows_valid,
+                                                          const uint8_t* __restrict__ mask,
+                                                          uint32_t* __restrict__ img,
+                                                          int64_t row_words, int64_t words) {
+  constexpr int ROWS = 128, CH = 64, PITCH = ROWS + 8;  // bytes per channel row of the tile
+  __shared__ __align__(16) uint8_t tile[CH * PITCH];
+  const int64_t w0 = (int64_t)blockIdx.x * 64;  // first image word
+  const int cb0 = blockIdx.y * CH;               // first channel
+  const int64_t r0 = t_begin + w0 * 2 - kPad;    // raw row of the block's first sample
+  for (int e = threadIdx.x; e < ROWS * 4; e += 256) {
+    const int rr = e & (ROWS - 1);
+    const int pc = e >> 7;  // 16-channel piece of the row
+    const int64_t r = r0 + rr;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (r >= t_begin && r < t_begin + nrows_valid)
+      v = __ldg(reinterpret_cast<const uint4*>(in + r * in_stride + cb0 + 16 * pc));
+    const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        tile[(16 * pc + 4 * q + k) * PITCH + rr] = (uint8_t)(x[q] >> (8 * k));
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < CH * 16; e += 256) {
+    const int cl = e >> 4;
+    const int qd = e & 15;
+    const int64_t w = w0 + 4 * qd;
+    if (w >= words) continue;
+    const uint2 s = *reinterpret_cast<const uint2*>(&tile[cl * PITCH + 8 * qd]);
+    // samples 2i and 2i+1 into the low and high 16-bit lanes of word i
+    uint4 o = make_uint4(__byte_perm(s.x, 0u, 0x4140), __byte_perm(s.x, 0u, 0x4342),
+                         __byte_perm(s.y, 0u, 0x4140), __byte_perm(s.y, 0u, 0x4342));
+    const int c = cb0 + cl;
+    if (mask && mask[c] == 0) o = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(img + (int64_t)c * row_words + w) = o;
+  }
+}
+
 cudaError_t launch_corner_turn(int nbits, const uint8_t* in, int64_t in_stride, int64_t t_begin,
                                int64_t nrows_valid, int nchans, const uint8_t* mask,
                                uint32_t* img, int64_t row_words, int64_t words,
@@ -192,6 +241,14 @@ cudaError_t launch_corner_turn(int nbits, const uint8_t* in, int64_t in_stride, 
       !(in_stride & 15)) {
     const dim3 g2((unsigned)((words + 31) / 32), (unsigned)(nchans / 128));
     k_corner_turn_2bit<<<g2, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img,
+                                           row_words, words);
+    return cudaGetLastError();
+  }
+  if (nbits == 8 && nchans % 64 == 0 && !(reinterpret_cast<uintptr_t>(in) & 15) &&
+      !(in_stride & 15) && !(row_words & 3) && !(words & 3) &&
+      !(reinterpret_cast<uintptr_t>(img) & 15)) {
+    const dim3 g8((unsigned)((words + 63) / 64), (unsigned)(nchans / 64));
+    k_corner_turn_8bit<<<g8, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, mask, img,
                                            row_words, words);
     return cudaGetLastError();
   }

@@ -70,7 +70,8 @@ def test_float_input_within_tolerance(orc):
     assert np.all(err <= F32_TOL * ab), float((err / ab).max())
 
 
-def test_killmask_bit_exact(orc):
+@pytest.mark.parametrize("nbits", [2, 8])
+def test_killmask_bit_exact(orc, nbits):
     plan = _survey_plan(step=40)
     mask = np.ones(1024, np.uint8)
     mask[[0, 1, 2, 100, 511, 512, 1000, 1023]] = 0
@@ -78,9 +79,9 @@ def test_killmask_bit_exact(orc):
     plan.set_killmask(mask)
     nsamps = 2000
     rows = nsamps + plan.max_delay
-    x = synth.uniform_packed(5, 0, rows, 1024, 2)
-    got, _ = run_direct(plan, x, 2, nsamps)
-    assert np.array_equal(got, orc.direct(x, 2, 1024, nsamps, odelays(orc, plan), mask))
+    x = synth.uniform_packed(5, 0, rows, 1024, nbits)
+    got, _ = run_direct(plan, x, nbits, nsamps)
+    assert np.array_equal(got, orc.direct(x, nbits, 1024, nsamps, odelays(orc, plan), mask))
 
 
 @pytest.mark.parametrize("nchans,ndm,nsamps,nbits", [
