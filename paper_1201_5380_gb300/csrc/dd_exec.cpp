@@ -171,6 +171,7 @@ static dd_status build_stage_tab(const TabSrc& src, int fmt, int cfg, int cc_cap
   t->atab.assign((size_t)(t->g_atab * src.ngroups), 0u);
   t->crec.assign((size_t)(t->g_crec * src.ngroups), 0);
   t->smem = 0;
+  t->reach = 0;
   // window start of (block, channel) and the words its trials read
   auto window = [&](const int32_t* dl, int d0, int d1, int c, int64_t* woff,
                     int64_t* span) -> bool {
@@ -258,6 +259,8 @@ static dd_status build_stage_tab(const TabSrc& src, int fmt, int cfg, int cc_cap
         }
         cr[2 * c] = (int32_t)woff;
         cr[2 * c + 1] = (int32_t)span;
+        // a copy reads at most span + 7 words from woff
+        t->reach = std::max<int64_t>(t->reach, woff + span + 8);
       }
     }
   }
@@ -511,21 +514,15 @@ static bool device_range_ok(const void* ptr, size_t bytes) {
   return (unsigned long long)(uintptr_t)ptr + bytes <= base + size;
 }
 
-// Corner-turn `rows` input rows into `image` (grown as needed); fills the
-// staged-image fields of a direct job for nsamps outputs.
-dd_status stage_direct_image(Plan& p, const void* in, int nbits, int64_t in_stride, int64_t rows,
-                             int64_t nsamps, DevBuf& image, cudaStream_t st, DirectJob* j) {
+// The staged image of a direct job for nsamps outputs: `image` grown as
+// needed, the job's image fields filled; nothing launched.
+static dd_status prepare_direct_image(Plan& p, int nbits, int64_t nsamps, DevBuf& image,
+                                      DirectJob* j) {
   const int fmt = fmt_for_nbits(nbits);
   const int64_t rw = direct_row_words(p, fmt, nsamps);
   cudaError_t e = image.ensure((size_t)p.nchans * rw * 4);
   if (e != cudaSuccess) return cuda_status(e);
   uint32_t* img = static_cast<uint32_t*>(image.p);
-  {
-    KernelTimer kt(&p, 0, st);
-    e = launch_corner_turn(nbits, static_cast<const uint8_t*>(in), in_stride, 0, rows, p.nchans,
-                           static_cast<const uint8_t*>(p.d_mask.p), img, rw, rw, st);
-  }
-  if (e != cudaSuccess) return cuda_status(e);
   j->img = img;
   j->row_words = rw;
   j->img_row_samples = rw * fmt_spw(fmt);
@@ -536,6 +533,19 @@ dd_status stage_direct_image(Plan& p, const void* in, int nbits, int64_t in_stri
   j->nsamps = nsamps;
   j->plan = &p;
   return DD_OK;
+}
+
+// Corner-turn `rows` input rows into `image` (grown as needed); fills the
+// staged-image fields of a direct job for nsamps outputs.
+dd_status stage_direct_image(Plan& p, const void* in, int nbits, int64_t in_stride, int64_t rows,
+                             int64_t nsamps, DevBuf& image, cudaStream_t st, DirectJob* j) {
+  dd_status s = prepare_direct_image(p, nbits, nsamps, image, j);
+  if (s != DD_OK) return s;
+  KernelTimer kt(&p, 0, st);
+  return cuda_status(launch_corner_turn(nbits, static_cast<const uint8_t*>(in), in_stride, 0, rows,
+                                        p.nchans, static_cast<const uint8_t*>(p.d_mask.p),
+                                        const_cast<uint32_t*>(j->img), j->row_words, 0,
+                                        j->row_words, st));
 }
 
 static dd_status exec_direct(Plan& p, const ExecArgs& a, int fmt) {
@@ -553,14 +563,22 @@ static dd_status exec_direct(Plan& p, const ExecArgs& a, int fmt) {
   return run_launch(p, L, a.st);
 }
 
-// Direct transform into host memory.  The time tiles run as kOutParts
-// launches, each over every trial block, so that the blocks of a tile still
-// share its staged windows in L2 as in one launch (parts by trial block lose
-// that reuse and ran 13 % slower in total).  Each part's output columns, all
-// rows, are copied to the host on a second stream while the next part
-// computes; the parts shrink towards the end so that little copying is left
-// once the last kernel ends.  Synchronises.
-static dd_status exec_direct_host_out(Plan& p, const ExecArgs& a, int fmt, void* host_out) {
+// Direct transform from and into host memory.  The time tiles run as
+// kOutParts launches, each over every trial block, so that the blocks of a
+// tile still share its staged windows in L2 as in one launch (parts by
+// trial block lose that reuse and ran 13 % slower in total).
+//
+// - Input: each part needs the image words its tiles' windows reach, which
+//   need a prefix of the input rows.  Those rows are copied in on a second
+//   stream piece by piece and corner-turned just before the part, so only
+//   the first part waits for its rows; the rest arrive while it computes.
+// - Output: each part's output columns, all rows, are copied to the host on
+//   a third stream while the next part computes; the parts shrink towards
+//   the end so that little copying is left once the last kernel ends.
+//
+// Synchronises.
+static dd_status exec_direct_host_out(Plan& p, const ExecArgs& a, int fmt, const void* host_in,
+                                      size_t in_bytes, void* host_out) {
   // part ends, in thousandths of the tiles
   constexpr int kOutParts = 8;
   static const int kPartEnd[kOutParts] = {160, 320, 480, 640, 800, 900, 960, 1000};
@@ -568,33 +586,68 @@ static dd_status exec_direct_host_out(Plan& p, const ExecArgs& a, int fmt, void*
   if (s != DD_OK) return s;
   const int64_t rows = a.nsamps_out + p.max_delay;
   DirectJob j;
-  if ((s = stage_direct_image(p, a.in, a.in_nbits, a.in_row_stride, rows, a.nsamps_out,
-                              p.d_image, a.st, &j)) != DD_OK)
-    return s;
+  if ((s = prepare_direct_image(p, a.in_nbits, a.nsamps_out, p.d_image, &j)) != DD_OK) return s;
   j.out = a.out;
   j.out_stride = a.out_stride;
   LaunchPlan L;
+  std::vector<StageTab*> tabs;
   if ((s = plan_direct_launch(p, fmt, fmt == FMT_F32 ? OUT_F32 : OUT_U32,
-                              vmax_for_nbits(a.in_nbits), {j}, &L)) != DD_OK)
+                              vmax_for_nbits(a.in_nbits), {j}, &L, &tabs)) != DD_OK)
     return s;
   cudaError_t e = cudaSuccess;
   if (!p.copy_st) e = cudaStreamCreateWithFlags(&p.copy_st, cudaStreamNonBlocking);
-  while (e == cudaSuccess && p.part_ev.size() < (size_t)kOutParts) {
+  if (e == cudaSuccess && !p.in_st) e = cudaStreamCreateWithFlags(&p.in_st, cudaStreamNonBlocking);
+  while (e == cudaSuccess && p.part_ev.size() < (size_t)(2 * kOutParts + 1)) {
     cudaEvent_t ev = nullptr;
     e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) p.part_ev.push_back(ev);
   }
   if (e != cudaSuccess) return cuda_status(e);
   const Seg g = L.lp.segs[0];
+  const int spw = fmt_spw(fmt);
   const int64_t T = time_tile(fmt, tuning_for(p.tune, fmt));
   const int64_t tiles = (g.nsamps + T - 1) / T;
   const int64_t per_tile = (int64_t)g.n_groups * g.n_dmblk;
+  const int64_t rw = j.row_words;
+  const int64_t reach = tabs.empty() || !tabs[0] ? rw : tabs[0]->reach;
   const int esz = out_elem_bytes(p, fmt == FMT_F32 ? OUT_F32 : OUT_U32);
   const size_t pitch = (size_t)a.out_stride * esz;
-  int64_t t0 = 0;
+  const size_t stride = (size_t)a.in_row_stride;
+  uint8_t* const d_in = static_cast<uint8_t*>(const_cast<void*>(a.in));
+  // the input stream starts after the caller's earlier work on a.st
+  if ((e = cudaEventRecord(p.part_ev[2 * kOutParts], a.st)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(p.in_st, p.part_ev[2 * kOutParts], 0)) != cudaSuccess)
+    return cuda_status(e);
+  int64_t t0 = 0, w_done = 0, r_done = 0;
   for (int q = 0; q < kOutParts; ++q) {
     const int64_t t1 = tiles * kPartEnd[q] / 1000;
     if (t1 <= t0) continue;
+    // image words this part's windows reach (whole 64-word pieces), and the
+    // input rows those words are made from
+    int64_t w_need = t1 >= tiles ? rw : std::min(rw, ((t1 * T / spw + reach + 63) / 64) * 64);
+    if (w_need > w_done) {
+      const int64_t r_need =
+          w_need >= rw ? rows : std::min(rows, std::max<int64_t>(0, w_need * spw - kPad));
+      if (r_need > r_done) {
+        const size_t b0 = (size_t)r_done * stride;
+        const size_t b1 = r_need >= rows ? in_bytes : std::min(in_bytes, (size_t)r_need * stride);
+        if (b1 > b0 &&
+            ((e = cudaMemcpyAsync(d_in + b0, static_cast<const uint8_t*>(host_in) + b0, b1 - b0,
+                                  cudaMemcpyHostToDevice, p.in_st)) != cudaSuccess ||
+             (e = cudaEventRecord(p.part_ev[kOutParts + q], p.in_st)) != cudaSuccess ||
+             (e = cudaStreamWaitEvent(a.st, p.part_ev[kOutParts + q], 0)) != cudaSuccess))
+          return cuda_status(e);
+        r_done = r_need;
+      }
+      {
+        KernelTimer kt(&p, 0, a.st);
+        e = launch_corner_turn(a.in_nbits, d_in, a.in_row_stride, 0, rows, p.nchans,
+                               static_cast<const uint8_t*>(p.d_mask.p),
+                               const_cast<uint32_t*>(j.img), rw, w_done, w_need, a.st);
+      }
+      if (e != cudaSuccess) return cuda_status(e);
+      w_done = w_need;
+    }
     LaunchPlan Lq = L;
     Lq.lp.segs[0].tile0 = t0;
     Lq.lp.n_items = (t1 - t0) * per_tile;
@@ -643,7 +696,8 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
   {
     KernelTimer kt(&p, 0, a.st);
     e = launch_corner_turn(a.in_nbits, static_cast<const uint8_t*>(a.in), a.in_row_stride, 0,
-                           rows, C, static_cast<const uint8_t*>(p.d_mask.p), img, rw, rw, a.st);
+                           rows, C, static_cast<const uint8_t*>(p.d_mask.p), img, rw, 0, rw,
+                           a.st);
   }
   if (e != cudaSuccess) return cuda_status(e);
 
@@ -800,11 +854,11 @@ extern "C" dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void* in
   cudaError_t e;
   if ((e = p->d_in.ensure(in_bytes)) != cudaSuccess) return cuda_status(e);
   if ((e = p->d_out.ensure(out_bytes)) != cudaSuccess) return cuda_status(e);
-  if ((e = cudaMemcpyAsync(p->d_in.p, in, in_bytes, cudaMemcpyHostToDevice, a.st)) != cudaSuccess)
-    return cuda_status(e);
   a.in = p->d_in.p;
   a.out = p->d_out.p;
-  if (!sub) return exec_direct_host_out(*p, a, fmt, out);
+  if (!sub) return exec_direct_host_out(*p, a, fmt, in, in_bytes, out);
+  if ((e = cudaMemcpyAsync(p->d_in.p, in, in_bytes, cudaMemcpyHostToDevice, a.st)) != cudaSuccess)
+    return cuda_status(e);
   dd_status s = exec_device(*p, a);
   if (s != DD_OK) return s;
   if ((e = cudaMemcpy2DAsync(out, (size_t)out_stride * esz, p->d_out.p,

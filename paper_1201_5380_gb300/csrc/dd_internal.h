@@ -138,10 +138,11 @@ cudaError_t launch_dedisp(int fmt, int outk, bool wide, int cfg, const LaunchPar
                           int grid, size_t smem, cudaStream_t st);
 cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, bool pbg, size_t smem,
                                      int* nblk);
+// Image words [w_first, words) of every channel row.
 cudaError_t launch_corner_turn(int nbits, const uint8_t* in, int64_t in_stride,
                                int64_t t_begin, int64_t nrows_valid, int nchans,
                                const uint8_t* mask, uint32_t* img, int64_t row_words,
-                               int64_t words, cudaStream_t st);
+                               int64_t w_first, int64_t words, cudaStream_t st);
 
 size_t dedisp_smem_bytes(int fmt, int cfg, int cc, int nww);
 cudaError_t launch_probe(const uint32_t* seed, int64_t iters, uint32_t* sink, int grid,
@@ -176,6 +177,7 @@ struct StageTab {
   size_t smem = 0;             // dynamic shared memory of the widest block
   bool uniform = false;        // every block has chunk geometry (cc, nww)
   int cc = 0, nww = 0;
+  int64_t reach = 0;           // image words past t0/SPW that any tile's windows read
   DevBuf d_atab, d_crec;
 };
 
@@ -251,7 +253,8 @@ struct Plan {
   std::vector<int32_t> scr_factor;  // per trial
   DevBuf d_scr;                     // scrunched input of the level being run
   // host-pointer execute: output copies overlap the next part's compute
-  cudaStream_t copy_st = nullptr;
+  cudaStream_t copy_st = nullptr;  // host-output path: copies out
+  cudaStream_t in_st = nullptr;    // host-output path: input rows in
   std::vector<cudaEvent_t> part_ev;
   uint32_t launch_seq = 0;  // round-robin index into the item counters
   std::mutex mu;

@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(256) k_corner_turn(const uint8_t* __restrict__
                                                      int64_t nrows_valid, int nchans,
                                                      const uint8_t* __restrict__ mask,
                                                      uint32_t* __restrict__ img,
-                                                     int64_t row_words, int64_t words) {
+                                                     int64_t row_words, int64_t w_first,
+                                                     int64_t words) {
   constexpr bool F32 = (NBITS == 32);
   constexpr int SPW = F32 ? 1 : (NBITS <= 2 ? 8 : (NBITS == 4 ? 4 : 2));
   constexpr int LW = 32 / SPW;
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(256) k_corner_turn(const uint8_t* __restrict__
   constexpr int PITCH = ROWB + 4;
   __shared__ uint8_t tile[R * PITCH];
 
-  const int64_t w0 = (int64_t)blockIdx.x * WB;
+  const int64_t w0 = w_first + (int64_t)blockIdx.x * WB;
   const int cb0 = blockIdx.y * CB;
   const int64_t rbytes = F32 ? (int64_t)nchans * 4 : ((int64_t)nchans * NBITS + 7) / 8;
   const int64_t b0 = F32 ? (int64_t)cb0 * 4 : (int64_t)cb0 * NBITS / 8;
@@ -136,10 +137,11 @@ __global__ void __launch_bounds__(256) k_corner_turn_2bit(const uint8_t* __restr
                                                           int64_t nrows_valid, int nchans,
                                                           const uint8_t* __restrict__ mask,
                                                           uint32_t* __restrict__ img,
-                                                          int64_t row_words, int64_t words) {
+                                                          int64_t row_words, int64_t w_first,
+                                                          int64_t words) {
   constexpr int ROWS = 256, COLS = 32, PITCH = ROWS + 8;  // bytes per byte-column row
   __shared__ __align__(16) uint8_t tile[COLS * PITCH];
-  const int64_t w0 = (int64_t)blockIdx.x * 32;     // first image word
+  const int64_t w0 = w_first + (int64_t)blockIdx.x * 32;  // first image word
   const int cb0 = blockIdx.y * 128;                // first channel
   const int64_t r0 = t_begin + w0 * 8 - kPad;      // raw row of the block's first sample
   {
@@ -192,10 +194,11 @@ __global__ void __launch_bounds__(256) k_corner_turn_8bit(const uint8_t* __restr
                                                           int64_t nrows_valid,
                                                           const uint8_t* __restrict__ mask,
                                                           uint32_t* __restrict__ img,
-                                                          int64_t row_words, int64_t words) {
+                                                          int64_t row_words, int64_t w_first,
+                                                          int64_t words) {
   constexpr int ROWS = 128, CH = 64, PITCH = ROWS + 8;  // bytes per channel row of the tile
   __shared__ __align__(16) uint8_t tile[CH * PITCH];
-  const int64_t w0 = (int64_t)blockIdx.x * 64;  // first image word
+  const int64_t w0 = w_first + (int64_t)blockIdx.x * 64;  // first image word
   const int cb0 = blockIdx.y * CH;               // first channel
   const int64_t r0 = t_begin + w0 * 2 - kPad;    // raw row of the block's first sample
   for (int e = threadIdx.x; e < ROWS * 4; e += 256) {
@@ -230,34 +233,36 @@ __global__ void __launch_bounds__(256) k_corner_turn_8bit(const uint8_t* __restr
 
 cudaError_t launch_corner_turn(int nbits, const uint8_t* in, int64_t in_stride, int64_t t_begin,
                                int64_t nrows_valid, int nchans, const uint8_t* mask,
-                               uint32_t* img, int64_t row_words, int64_t words,
+                               uint32_t* img, int64_t row_words, int64_t w_first, int64_t words,
                                cudaStream_t st) {
   const int CB = nbits == 32 ? 32 : 256 / nbits;
   const int WB = nbits == 32 ? 64 : 32;
-  dim3 grid((unsigned)((words + WB - 1) / WB), (unsigned)((nchans + CB - 1) / CB));
+  if (w_first < 0 || w_first >= words) return cudaSuccess;
+  const int64_t n = words - w_first;
+  dim3 grid((unsigned)((n + WB - 1) / WB), (unsigned)((nchans + CB - 1) / CB));
   if (grid.x == 0 || grid.y == 0) return cudaSuccess;
   if (grid.y > 65535) return cudaErrorInvalidValue;
   if (nbits == 2 && nchans % 128 == 0 && !(reinterpret_cast<uintptr_t>(in) & 15) &&
       !(in_stride & 15)) {
-    const dim3 g2((unsigned)((words + 31) / 32), (unsigned)(nchans / 128));
+    const dim3 g2((unsigned)((n + 31) / 32), (unsigned)(nchans / 128));
     k_corner_turn_2bit<<<g2, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img,
-                                           row_words, words);
+                                           row_words, w_first, words);
     return cudaGetLastError();
   }
   if (nbits == 8 && nchans % 64 == 0 && !(reinterpret_cast<uintptr_t>(in) & 15) &&
-      !(in_stride & 15) && !(row_words & 3) && !(words & 3) &&
+      !(in_stride & 15) && !(row_words & 3) && !(w_first & 3) && !(words & 3) &&
       !(reinterpret_cast<uintptr_t>(img) & 15)) {
-    const dim3 g8((unsigned)((words + 63) / 64), (unsigned)(nchans / 64));
+    const dim3 g8((unsigned)((n + 63) / 64), (unsigned)(nchans / 64));
     k_corner_turn_8bit<<<g8, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, mask, img,
-                                           row_words, words);
+                                           row_words, w_first, words);
     return cudaGetLastError();
   }
   switch (nbits) {
-    case 1: k_corner_turn<1><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, words); break;
-    case 2: k_corner_turn<2><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, words); break;
-    case 4: k_corner_turn<4><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, words); break;
-    case 8: k_corner_turn<8><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, words); break;
-    case 32: k_corner_turn<32><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, words); break;
+    case 1: k_corner_turn<1><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
+    case 2: k_corner_turn<2><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
+    case 4: k_corner_turn<4><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
+    case 8: k_corner_turn<8><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
+    case 32: k_corner_turn<32><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

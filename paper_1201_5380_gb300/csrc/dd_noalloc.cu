@@ -130,7 +130,7 @@ extern "C" dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const 
 
   const int64_t rows = nsamps_out + p->max_delay;
   e = launch_corner_turn(in_nbits, static_cast<const uint8_t*>(in), in_row_stride, 0, rows,
-                         p->nchans, mask, img, rw, rw, st);
+                         p->nchans, mask, img, rw, 0, rw, st);
   if (e != cudaSuccess) return cuda_status(e);
 
   Seg& g = L.lp.segs[0];

@@ -60,6 +60,7 @@ Plan::~Plan() {
   drain_timing(*this);
   for (cudaEvent_t e : part_ev) cudaEventDestroy(e);
   if (copy_st) cudaStreamDestroy(copy_st);
+  if (in_st) cudaStreamDestroy(in_st);
 }
 
 KernelTimer::KernelTimer(Plan* plan, int k, cudaStream_t s) : p(plan), kind(k), st(s) {

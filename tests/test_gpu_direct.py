@@ -141,6 +141,27 @@ def test_host_pointer_path_in_parts_with_padded_rows(orc):
     assert np.all(out[:, nsamps:] == 0xDEADBEEF)
 
 
+@pytest.mark.parametrize("nbits", [1, 8, 32])
+def test_host_pointer_path_formats_in_parts(orc, nbits):
+    """Host buffers, several parts: the input rows arrive piece by piece and
+    are corner-turned just before the part that needs them."""
+    torch_cuda()
+    plan = _survey_plan(hi=2000.0, step=12)
+    nsamps = 7000
+    rows = nsamps + plan.max_delay
+    if nbits == 32:
+        x = synth.normal_f32(31, 0, rows, 1024)
+        out = np.zeros((plan.dm_count, nsamps), np.float32)
+        plan.execute(x, 32, nsamps, out)
+        ref, ab = orc.direct_f32(x, nsamps, odelays(orc, plan))
+        assert np.all(np.abs(out.astype(np.float64) - ref) <= F32_TOL * ab)
+        return
+    x = synth.uniform_packed(31, nbits, rows, 1024, nbits)
+    out = np.zeros((plan.dm_count, nsamps), np.uint32)
+    plan.execute(x, nbits, nsamps, out)
+    assert np.array_equal(out, orc.direct(x, nbits, 1024, nsamps, odelays(orc, plan)))
+
+
 @pytest.mark.parametrize("tiling", [(32, 4, 4), (32, 8, 4), (32, 16, 4), (32, 32, 4), (16, 32, 4),
                                     (64, 8, 2), (64, 4, 2),
                                     (16, 4, 4), (16, 8, 4), (32, 4, 2), (32, 8, 2), (32, 16, 2),
