@@ -48,6 +48,11 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-subband", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default tiling instead of the autotuner's choice")
+    ap.add_argument("--tiling", default="",
+                    help="trials per block, channel cap, words per lane (e.g. 64,16,2): a "
+                         "fixed tiling instead of the autotuner's (for profiler captures)")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the format sweep (1/4/8-bit and float input)")
     ap.add_argument("--nbits", type=int, default=2, choices=[1, 2, 4, 8],
@@ -135,8 +140,8 @@ class ClockSampler:
 # 2^17 output samples, from ncu, per (input bits, largest trial DM), with the
 # summary that holds the capture; the traffic grows in proportion to the gulp.
 DEDISP_TRAFFIC_2E17 = {
-    (2, 1000.0): (77.189632e6 + 568.246016e6, "profiles/k_dedisp_survey_ncu_full.md"),
-    (8, 2000.0): (470.875136e6 + 732.305664e6, "profiles/k_dedisp_8bit_dm2000_ncu_full.md"),
+    (2, 1000.0): (76.863232e6 + 568.540416e6, "profiles/k_dedisp_survey_ncu_full.md"),
+    (8, 2000.0): (467.081472e6 + 731.687168e6, "profiles/k_dedisp_8bit_dm2000_ncu_full.md"),
 }
 
 
@@ -681,6 +686,12 @@ def run_ours(a, rank, world, local_rank):
     nb = a.nbits
     plan = dd.Plan(nchans, c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=a.dm_hi),
                    gulp=G)
+    if a.tiling:
+        plan.set_tuning(*[int(v) for v in a.tiling.split(",")])
+    elif not a.no_autotune:
+        # the library's tiling search (every compiled tile shape x chunk cap,
+        # timed on a 2^17-sample gulp of this plan), as a user would run once
+        plan.autotune(nb, 1 << 17)
     ndm = plan.dm_count
     delays = plan.delay_table()
     x = _make_input(plan.dms, delays, G, plan.max_delay, nb)

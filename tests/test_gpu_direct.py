@@ -176,13 +176,20 @@ def test_every_tiling_bit_exact(orc, tiling):
     assert np.array_equal(got, orc.direct(x, 2, 1024, nsamps, odelays(orc, plan)))
 
 
-def test_survey_full_size_sampled(orc):
+@pytest.mark.parametrize("tiling", ["default", "autotune", (64, 16, 2)])
+def test_survey_full_size_sampled(orc, tiling):
     """Config at full size (1024 ch, 2-bit, 1196 trials, 2^19 samples), in the
-    launch configuration the benchmark times; sampled points + the pulses."""
+    launch configurations the benchmark times (default tiling, the
+    autotuner's choice, the one it picks on this workload); sampled points +
+    the pulses."""
     torch = torch_cuda()
     c = configs.SURVEY
     plan = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
     assert plan.dm_count == 1196
+    if tiling == "autotune":
+        plan.autotune(2, 1 << 17)
+    elif tiling != "default":
+        plan.set_tuning(*tiling)
     G = c["nsamps"]
     rows = G + plan.max_delay
     delays = odelays(orc, plan)
