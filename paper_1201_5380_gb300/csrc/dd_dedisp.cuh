@@ -532,12 +532,31 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
           (COPIES ? smem_addr(copies + buf * copy_words) : smem_addr(landing + buf * landing_words)) +
           (uint32_t)lane * 4u;
       bool paired = false;
-      if constexpr (FMT == FMT_NIB) paired = p.f0 == 1 && p.f1 >= 2 && (cc & 7) == 0;
+      if constexpr (FMT == FMT_NIB)
+        paired = p.f0 == 1 && p.f1 >= 2 && (cc & 7) == 0 && (cc >> 3) <= (p.f1 >> 1);
       if (paired) {
         // 2-bit input: pairs of 4-channel groups widened together; a pair
-        // adds at most two group sums to a byte lane, so the 16-bit flush
-        // comes every f1/2 pairs
-        if constexpr (FMT == FMT_NIB)
+        // adds at most two group sums to a byte lane, so byte lanes take
+        // f1/2 pairs between 16-bit flushes.  The flush is taken before a
+        // chunk whose pairs would pass that, so the pair loop itself has no
+        // branch.
+        if constexpr (FMT == FMT_NIB) {
+        const int npairs = cc >> 3;
+        if (g1 + npairs > (p.f1 >> 1)) {
+          g1 = 0;
+#pragma unroll
+          for (int i = 0; i < DPW; ++i)
+#pragma unroll
+            for (int j = 0; j < K; ++j) acc[i][j].flush1();
+          if (WIDE && ++g2 == p.f2) {
+            g2 = 0;
+#pragma unroll
+            for (int i = 0; i < DPW; ++i)
+#pragma unroll
+              for (int j = 0; j < K; ++j) acc[i][j].flush2();
+          }
+        }
+        g1 += npairs;
         for (int cg = 0; cg < cc; cg += 8) {
 #pragma unroll
           for (int i = 0; i < DPW; ++i) {
@@ -555,20 +574,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
                                    lds32(q4 + 128u * j), lds32(q5 + 128u * j),
                                    lds32(q6 + 128u * j), lds32(q7 + 128u * j));
           }
-          if (++g1 == (p.f1 >> 1)) {
-            g1 = 0;
-#pragma unroll
-            for (int i = 0; i < DPW; ++i)
-#pragma unroll
-              for (int j = 0; j < K; ++j) acc[i][j].flush1();
-            if (WIDE && ++g2 == p.f2) {
-              g2 = 0;
-#pragma unroll
-              for (int i = 0; i < DPW; ++i)
-#pragma unroll
-                for (int j = 0; j < K; ++j) acc[i][j].flush2();
-            }
-          }
+        }
         }
       } else
       for (int cg = 0; cg < cc; cg += 4) {
