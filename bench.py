@@ -140,7 +140,7 @@ class ClockSampler:
 # 2^17 output samples, from ncu, per (input bits, largest trial DM), with the
 # summary that holds the capture; the traffic grows in proportion to the gulp.
 DEDISP_TRAFFIC_2E17 = {
-    (2, 1000.0): (76.863232e6 + 568.540416e6, "profiles/k_dedisp_survey_ncu_full.md"),
+    (2, 1000.0): (76.975872e6 + 568.535296e6, "profiles/k_dedisp_survey_ncu_full.md"),
     (8, 2000.0): (467.081472e6 + 731.687168e6, "profiles/k_dedisp_8bit_dm2000_ncu_full.md"),
 }
 
