@@ -541,40 +541,40 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
         // chunk whose pairs would pass that, so the pair loop itself has no
         // branch.
         if constexpr (FMT == FMT_NIB) {
-        const int npairs = cc >> 3;
-        if (g1 + npairs > (p.f1 >> 1)) {
-          g1 = 0;
-#pragma unroll
-          for (int i = 0; i < DPW; ++i)
-#pragma unroll
-            for (int j = 0; j < K; ++j) acc[i][j].flush1();
-          if (WIDE && ++g2 == p.f2) {
-            g2 = 0;
+          const int npairs = cc >> 3;
+          if (g1 + npairs > (p.f1 >> 1)) {
+            g1 = 0;
 #pragma unroll
             for (int i = 0; i < DPW; ++i)
 #pragma unroll
-              for (int j = 0; j < K; ++j) acc[i][j].flush2();
-          }
-        }
-        g1 += npairs;
-        for (int cg = 0; cg < cc; cg += 8) {
+              for (int j = 0; j < K; ++j) acc[i][j].flush1();
+            if (WIDE && ++g2 == p.f2) {
+              g2 = 0;
 #pragma unroll
-          for (int i = 0; i < DPW; ++i) {
-            const uint32_t* const e = sa + ((warp * DPW + i) << cc_log) + cg;
-            const uint4 a4 = *reinterpret_cast<const uint4*>(e);
-            const uint4 b4 = *reinterpret_cast<const uint4*>(e + 4);
-            const uint32_t q0 = a4.x + lane_off, q1 = a4.y + lane_off;
-            const uint32_t q2 = a4.z + lane_off, q3 = a4.w + lane_off;
-            const uint32_t q4 = b4.x + lane_off, q5 = b4.y + lane_off;
-            const uint32_t q6 = b4.z + lane_off, q7 = b4.w + lane_off;
+              for (int i = 0; i < DPW; ++i)
 #pragma unroll
-            for (int j = 0; j < K; ++j)
-              acc[i][j].add8_flush(lds32(q0 + 128u * j), lds32(q1 + 128u * j),
-                                   lds32(q2 + 128u * j), lds32(q3 + 128u * j),
-                                   lds32(q4 + 128u * j), lds32(q5 + 128u * j),
-                                   lds32(q6 + 128u * j), lds32(q7 + 128u * j));
+                for (int j = 0; j < K; ++j) acc[i][j].flush2();
+            }
           }
-        }
+          g1 += npairs;
+          for (int cg = 0; cg < cc; cg += 8) {
+#pragma unroll
+            for (int i = 0; i < DPW; ++i) {
+              const uint32_t* const e = sa + ((warp * DPW + i) << cc_log) + cg;
+              const uint4 a4 = *reinterpret_cast<const uint4*>(e);
+              const uint4 b4 = *reinterpret_cast<const uint4*>(e + 4);
+              const uint32_t q0 = a4.x + lane_off, q1 = a4.y + lane_off;
+              const uint32_t q2 = a4.z + lane_off, q3 = a4.w + lane_off;
+              const uint32_t q4 = b4.x + lane_off, q5 = b4.y + lane_off;
+              const uint32_t q6 = b4.z + lane_off, q7 = b4.w + lane_off;
+#pragma unroll
+              for (int j = 0; j < K; ++j)
+                acc[i][j].add8_flush(lds32(q0 + 128u * j), lds32(q1 + 128u * j),
+                                     lds32(q2 + 128u * j), lds32(q3 + 128u * j),
+                                     lds32(q4 + 128u * j), lds32(q5 + 128u * j),
+                                     lds32(q6 + 128u * j), lds32(q7 + 128u * j));
+            }
+          }
         }
       } else
       for (int cg = 0; cg < cc; cg += 4) {
