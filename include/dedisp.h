@@ -177,6 +177,18 @@ dd_status dd_plan_set_tuning(dd_plan plan, int dms_per_block, int chans_per_chun
 dd_status dd_plan_get_tuning(dd_plan plan, int *dms_per_block, int *chans_per_chunk,
                              int *words_per_lane);
 
+/* The chunk geometry of the direct kernel for in_nbits input under the
+ * plan's tiling, from its host-built staging tables (no device work): the
+ * number of trial blocks, and per block the channels staged per chunk and
+ * the window width in 32-bit words, then the launch's dynamic shared
+ * memory (its widest block's).  Each block stages as many channels (a power
+ * of two, 4 to the tiling's chunk cap) as its two staging buffers allow in
+ * shared memory; when all blocks get the same number they share one width.
+ * Pass null arrays to get n_blocks only; the arrays hold n_blocks entries. */
+dd_status dd_plan_get_chunk_geometry(dd_plan plan, int in_nbits, int32_t *n_blocks,
+                                     int32_t *chans_per_chunk, int32_t *window_words,
+                                     size_t *smem_bytes);
+
 /* Time every tiling candidate on nsamps_out synthetic samples of in_nbits
  * and keep the fastest (Sec. 2.3 and 4.3 tuned block shape by hand; this
  * searches the same kind of knobs).  Allocates temporary device buffers;

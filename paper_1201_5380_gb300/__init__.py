@@ -59,6 +59,8 @@ def _load_lib():
         "dd_plan_set_tuning": (I, [P, I, I, I]),
         "dd_plan_get_tuning": (I, [P, pp(I), pp(I), pp(I)]),
         "dd_plan_autotune": (I, [P, I, I64, P]),
+        "dd_plan_get_chunk_geometry": (I, [P, I, pp(ctypes.c_int32), P, P,
+                                           pp(ctypes.c_size_t)]),
         "dd_plan_get_dm_count": (I, [P, pp(ctypes.c_int32)]),
         "dd_plan_get_dm_list": (I, [P, P]),
         "dd_plan_get_max_delay": (I, [P, pp(ctypes.c_int32)]),
@@ -258,6 +260,22 @@ class Plan:
         _check(_lib.dd_plan_get_tuning(self._h, ctypes.byref(a), ctypes.byref(b),
                                        ctypes.byref(c)), "dd_plan_get_tuning")
         return dict(dms_per_block=a.value, chans_per_chunk=b.value, words_per_lane=c.value)
+
+    def chunk_geometry(self, nbits):
+        """Per trial block, the channels staged per chunk and the window width
+        (words) of the direct kernel for nbits input under the current
+        tiling, and the launch's dynamic shared memory; host-side only."""
+        n = ctypes.c_int32()
+        _check(_lib.dd_plan_get_chunk_geometry(self._h, int(nbits), ctypes.byref(n), None, None,
+                                               None), "dd_plan_get_chunk_geometry")
+        cc = np.zeros(n.value, np.int32)
+        nww = np.zeros(n.value, np.int32)
+        smem = ctypes.c_size_t()
+        _check(_lib.dd_plan_get_chunk_geometry(self._h, int(nbits), ctypes.byref(n),
+                                               cc.ctypes.data, nww.ctypes.data,
+                                               ctypes.byref(smem)),
+               "dd_plan_get_chunk_geometry")
+        return dict(chans_per_chunk=cc, window_words=nww, smem_bytes=smem.value)
 
     def autotune(self, nbits, nsamps, stream=None):
         _check(_lib.dd_plan_autotune(self._h, int(nbits), int(nsamps), _stream_ptr(stream)),

@@ -877,6 +877,38 @@ extern "C" dd_status dd_plan_set_output_bits(dd_plan plan, int bits) {
   return DD_OK;
 }
 
+extern "C" dd_status dd_plan_get_chunk_geometry(dd_plan plan, int in_nbits, int32_t* n_blocks,
+                                               int32_t* chans_per_chunk, int32_t* nww_out,
+                                               size_t* smem_bytes) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p || !n_blocks) return DD_ERR_INVALID_ARG;
+  const int fmt = fmt_for_nbits(in_nbits);
+  if (fmt < 0) return DD_ERR_UNSUPPORTED_NBITS;
+  if (p->dms.empty()) return DD_ERR_NO_DM_LIST;
+  std::lock_guard<std::mutex> lk(p->mu);
+  const Tuning t = tuning_for(p->tune, fmt);
+  const int cfg = tile_cfg_index(t);
+  const int bi = b_index(kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw);
+  const std::vector<int32_t>& bl = p->blocks_B[bi];
+  const int nblk = (int)bl.size() - 1;
+  *n_blocks = nblk;
+  if (!chans_per_chunk && !nww_out && !smem_bytes) return DD_OK;
+  int cc_cap = 4;
+  while (cc_cap * 2 <= p->tune.chans_per_chunk) cc_cap *= 2;
+  const TabSrc src{p->delays.data(), 0, p->nchans, p->nchans, 1, bl.data(), nblk, p->lo_B[bi]};
+  dd_status err;
+  StageTab* tab = stage_tab(*p, 0, src, fmt, cfg, cc_cap, window_words(fmt, t, p->spread_B[bi]),
+                            false, &err);
+  if (!tab) return err;
+  for (int b = 0; b < nblk; ++b) {
+    const int32_t* geo = tab->crec.data() + ((int64_t)nblk * p->nchans + b) * 2;
+    if (chans_per_chunk) chans_per_chunk[b] = geo[0];
+    if (nww_out) nww_out[b] = geo[1];
+  }
+  if (smem_bytes) *smem_bytes = tab->smem;
+  return DD_OK;
+}
+
 extern "C" dd_status dd_plan_get_input_rows(dd_plan plan, int64_t nsamps_out, unsigned flags,
                                            int64_t* rows) {
   Plan* p = reinterpret_cast<Plan*>(plan);

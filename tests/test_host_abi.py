@@ -172,3 +172,44 @@ def test_scrunch_input_rows_and_validation(orc):
         need = max(need, s * (G // s + m))
     assert p.input_rows(G, scrunch=True) == need
     assert p.input_rows(G) == G + p.max_delay
+
+
+def test_chunk_geometry_per_trial_block():
+    """The staging tables give each trial block its own chunk: as many
+    channels (a power of two up to the tiling's cap) as its windows leave
+    room for, so low-DM blocks stage more channels than the highest ones."""
+    from synth import configs
+    c = configs.SURVEY
+    p = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
+    g = p.chunk_geometry(2)
+    cc, nww = g["chans_per_chunk"], g["window_words"]
+    assert len(cc) == len(nww) >= (p.dm_count + 31) // 32
+    assert set(cc.tolist()) <= {4, 8, 16, 32}
+    assert np.all(nww > 0) and np.all(nww % 4 == 0)
+    assert 0 < g["smem_bytes"] <= 220 * 1024
+    # the window covers the tile (32 lanes x 4 words) plus the block's spread,
+    # which grows with DM; a narrower window never gets a smaller chunk
+    assert np.all(nww >= 32 * 4)
+    assert nww[-2] > nww[0] and cc[0] > cc[-2]
+    order = np.argsort(nww, kind="stable")
+    assert np.all(np.diff(cc[order]) <= 0)
+    # 64 trials per block: at most 1024 / 64 channels per chunk
+    p.set_tuning(64, 32, 2)
+    assert max(p.chunk_geometry(2)["chans_per_chunk"]) <= 16
+    # a small band with one narrow window everywhere: one geometry
+    t = dd.Plan(64, 64e-6, 1500.0, -1.0, dms=[float(i) for i in range(101)])
+    gt = t.chunk_geometry(8)
+    assert len(set(gt["chans_per_chunk"].tolist())) == 1
+    assert len(set(gt["window_words"].tolist())) == 1
+
+
+def test_chunk_geometry_8bit_wide_trials():
+    """8-bit input keeps two samples per word, so the highest trials' windows
+    (to DM 2000) leave room for only 4 channels, the lowest for 32."""
+    from synth import configs
+    c = configs.SURVEY
+    p = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=2000.0))
+    g = p.chunk_geometry(8)
+    assert g["chans_per_chunk"][0] == 32 and g["chans_per_chunk"][-1] == 4
+    with pytest.raises(dd.DedispError):
+        p.chunk_geometry(3)
