@@ -1,7 +1,9 @@
 // Direct dedispersion kernel (Sec. 2, Eq. 2) for sm_103a.
 //
 // One thread block owns a tile of B = NWARP*DPW adjacent trials x T output
-// samples of one work item and walks the channels in chunks of `cc`.  For
+// samples of one work item and walks the channels in chunks of `cc`, a size
+// the host picks per trial block (as many channels as the block's windows
+// leave room for in shared memory).  For
 // each chunk it stages, per channel, the window of the channel's image row
 // that any of its B trials needs (the temporal caching of Sec. 2.3, the
 // staged tile serving the whole trial block), as SPW copies shifted by one
@@ -441,7 +443,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
         wi = 0;
       }
       // the words this channel's trials read (plus the next word, which the
-      // lane-shift build reads), not the launch-wide window
+      // lane-shift build reads), not the block's whole window
       const int64_t want = min((int64_t)nwl, (int64_t)((r.y + 4 + 3) & ~3));
       const uint32_t words = has ? (uint32_t)min(want, row_words - wi) : 0u;
       const uint32_t tab_bytes = (uint32_t)n_entries * 4u;
