@@ -141,7 +141,7 @@ struct SegSpec {
   Plan* owner;     // plan that caches the staging tables
   TabSrc src;
   bool no_upload;  // tables stay on the host (the caller places them)
-  StageTab* tab;   // set by finish_launch
+  std::shared_ptr<StageTab> tab;  // set by finish_launch
 };
 
 // Staging tables (Seg::atab, Seg::crec) of one delay table.  For trial
@@ -267,18 +267,30 @@ static dd_status build_stage_tab(const TabSrc& src, int fmt, int cfg, int cc_cap
   return DD_OK;
 }
 
-StageTab* stage_tab(Plan& p, int kind, const TabSrc& src, int fmt, int cfg, int cc_cap,
-                    int nww_uniform, bool upload, dd_status* err) {
+std::shared_ptr<StageTab> stage_tab(Plan& p, int kind, const TabSrc& src, int fmt, int cfg,
+                                    int cc_cap, int nww_uniform, bool upload, dd_status* err) {
+  constexpr size_t kMaxTabs = 16;
   const std::array<int, 7> key = {kind, cfg, fmt, cc_cap, src.lo, nww_uniform, src.nblk};
+  std::shared_ptr<StageTab> t;
   auto it = p.tabs.find(key);
-  if (it == p.tabs.end()) {
-    if (p.tabs.size() >= 16) p.tabs.clear();  // bounded cache (frees synchronise the device)
-    std::unique_ptr<StageTab> t(new StageTab);
+  if (it != p.tabs.end()) {
+    t = it->second;
+  } else {
+    t = std::make_shared<StageTab>();
     *err = build_stage_tab(src, fmt, cfg, cc_cap, nww_uniform, t.get());
     if (*err != DD_OK) return nullptr;
-    it = p.tabs.emplace(key, std::move(t)).first;
+    if (p.tabs.size() < kMaxTabs) {
+      p.tabs.emplace(key, t);
+    } else if (upload) {
+      // Full: drop the cache's references.  A table still held elsewhere (a
+      // captured graph) lives on; the rest are freed here, which
+      // synchronises the device, so no launch in flight still reads them.
+      p.tabs.clear();
+      p.tabs.emplace(key, t);
+    }
+    // else: a host-only caller (no device allocation or free allowed) takes
+    // the table alone and the cache is left as it is
   }
-  StageTab* t = it->second.get();
   if (upload && !t->uploaded) {
     cudaError_t e = t->d_atab.ensure(t->atab.size() * 4);
     if (e == cudaSuccess)
@@ -381,9 +393,9 @@ static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector
     for (auto& sp : specs) {
       if (sp.seg.ndm <= 0 || sp.seg.nsamps <= 0) continue;
       dd_status err;
-      StageTab* t = stage_tab(*sp.owner, sp.kind, sp.src, fmt, cfg, cc_cap,
-                              window_words(fmt, tuning_for(p.tune, fmt), sp.spread),
-                              !sp.no_upload, &err);
+      std::shared_ptr<StageTab> t =
+          stage_tab(*sp.owner, sp.kind, sp.src, fmt, cfg, cc_cap,
+                    window_words(fmt, tuning_for(p.tune, fmt), sp.spread), !sp.no_upload, &err);
       if (!t) return err;
       // the kernel finds a block's geometry after the group's nblk x nchan
       // window records
@@ -431,7 +443,7 @@ dd_status run_launch(Plan& p, LaunchPlan& L, cudaStream_t st) {
 
 dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
                              const std::vector<DirectJob>& jobs, LaunchPlan* L,
-                             std::vector<StageTab*>* tabs) {
+                             std::vector<std::shared_ptr<StageTab>>* tabs) {
   const int cfg = tile_cfg_index(tuning_for(p.tune, fmt));
   const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
   std::vector<SegSpec> specs;
@@ -590,7 +602,7 @@ static dd_status exec_direct_host_out(Plan& p, const ExecArgs& a, int fmt, const
   j.out = a.out;
   j.out_stride = a.out_stride;
   LaunchPlan L;
-  std::vector<StageTab*> tabs;
+  std::vector<std::shared_ptr<StageTab>> tabs;
   if ((s = plan_direct_launch(p, fmt, fmt == FMT_F32 ? OUT_F32 : OUT_U32,
                               vmax_for_nbits(a.in_nbits), {j}, &L, &tabs)) != DD_OK)
     return s;
@@ -897,8 +909,8 @@ extern "C" dd_status dd_plan_get_chunk_geometry(dd_plan plan, int in_nbits, int3
   while (cc_cap * 2 <= p->tune.chans_per_chunk) cc_cap *= 2;
   const TabSrc src{p->delays.data(), 0, p->nchans, p->nchans, 1, bl.data(), nblk, p->lo_B[bi]};
   dd_status err;
-  StageTab* tab = stage_tab(*p, 0, src, fmt, cfg, cc_cap, window_words(fmt, t, p->spread_B[bi]),
-                            false, &err);
+  std::shared_ptr<StageTab> tab =
+      stage_tab(*p, 0, src, fmt, cfg, cc_cap, window_words(fmt, t, p->spread_B[bi]), false, &err);
   if (!tab) return err;
   for (int b = 0; b < nblk; ++b) {
     const int32_t* geo = tab->crec.data() + ((int64_t)nblk * p->nchans + b) * 2;

@@ -227,10 +227,13 @@ struct Plan {
   std::vector<int32_t> sb1_blk_B[3], sb2_blk_B[3];
   int32_t sb1_nblk_B[3] = {0, 0, 0}, sb2_nblk_B[3] = {0, 0, 0};
   DevBuf d_sb1_blk[3], d_sb2_blk[3];
-  // staging tables: key {kind (0 direct, 1/2 sub-band stage), B, SPW, K,
-  // cc, nww, lo_slack}.  An entry is never rebuilt in place (a launch on
-  // another stream may still read it); entries go when the delays change.
-  std::map<std::array<int, 7>, std::unique_ptr<StageTab>> tabs;
+  // staging tables: key {kind (0 direct, 1/2 sub-band stage), tile shape,
+  // format, chunk cap, lo_slack, window width, blocks}.  An entry is never
+  // rebuilt in place (a launch on another stream may still read it).  The
+  // cache is bounded: entries go when the delays change or when it is full
+  // and a launch needs a new uploaded table.  They are shared: a captured
+  // graph keeps the tables its kernels read alive however the cache changes.
+  std::map<std::array<int, 7>, std::shared_ptr<StageTab>> tabs;
   // kernel timing (dd_plan_set_kernel_timing)
   bool timing = false;
   struct TimedLaunch {
@@ -353,13 +356,15 @@ int out_elem_bytes(const Plan& p, int outk);
 bool out_vec_ok(const void* out, int64_t stride_elems, int esz);
 dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
                              const std::vector<DirectJob>& jobs, LaunchPlan* lpl,
-                             std::vector<StageTab*>* tabs = nullptr);
+                             std::vector<std::shared_ptr<StageTab>>* tabs = nullptr);
 dd_status run_launch(Plan& p, LaunchPlan& lpl, cudaStream_t st);
 // The plan's staging tables of `src` (kind 0 direct, 1/2 sub-band stage)
 // for a launch geometry, built on first use and uploaded when asked; null
-// with *err set if a window would not fit the geometry.
-StageTab* stage_tab(Plan& p, int kind, const TabSrc& src, int fmt, int cfg, int cc_cap,
-                    int nww_uniform, bool upload, dd_status* err);
+// with *err set if a window would not fit the geometry.  Without upload
+// nothing is allocated or freed on the device: a table not yet cached is
+// cached only while the cache has room, else returned to the caller alone.
+std::shared_ptr<StageTab> stage_tab(Plan& p, int kind, const TabSrc& src, int fmt, int cfg,
+                                    int cc_cap, int nww_uniform, bool upload, dd_status* err);
 void drop_stage_tabs(Plan& p, int kind_mask);
 dd_status stage_direct_image(Plan& p, const void* in, int nbits, int64_t in_stride, int64_t rows,
                              int64_t nsamps, DevBuf& image, cudaStream_t st, DirectJob* j);

@@ -89,12 +89,12 @@ extern "C" dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const 
   j.blk_dev = reinterpret_cast<const int32_t*>(sc);
   j.no_upload = true;
   LaunchPlan L;
-  std::vector<StageTab*> tabs;
+  std::vector<std::shared_ptr<StageTab>> tabs;
   s = plan_direct_launch(*p, fmt, fmt == FMT_F32 ? OUT_F32 : OUT_U32, vmax_for_nbits(in_nbits),
                          {j}, &L, &tabs);
   if (s != DD_OK) return s;
   if (L.lp.n_items == 0) return DD_OK;
-  const StageTab* t = tabs.at(0);
+  const std::shared_ptr<StageTab> t = tabs.at(0);
 
   // Layout of the scratch for this call; reject problems that do not fit.
   const size_t off_status = 0;

@@ -257,11 +257,15 @@ dd_status dd_batch_add(dd_batch b, dd_stream s, const void* in, int64_t n_in, in
   return DD_OK;
 }
 
+}  // extern "C"
+
 // All pushes of the batch: per-beam append + corner turn, then the whole
 // dedispersion of every beam in one persistent launch (one segment per beam,
 // each with its own image, delay table, channel count, trial count and gulp),
-// then per-beam tail retention.
-dd_status dd_batch_launch(dd_batch b, void* cuda_stream, int64_t* nsamps_out) {
+// then per-beam tail retention.  `hold` (optional) receives the staging
+// tables the launches read (a graph keeps them alive while it exists).
+static dd_status batch_launch(dd_batch b, void* cuda_stream, int64_t* nsamps_out,
+                              std::vector<std::shared_ptr<StageTab>>* hold) {
   if (!b || !nsamps_out) return DD_ERR_INVALID_ARG;
   if (b->items.empty()) return DD_OK;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -313,9 +317,11 @@ dd_status dd_batch_launch(dd_batch b, void* cuda_stream, int64_t* nsamps_out) {
       while (k1 < key.size() && part.size() < (size_t)kMaxSegs)
         part.push_back(jobs[key[k1++].job]);
       LaunchPlan L;
+      std::vector<std::shared_ptr<StageTab>> tabs;
       dd_status r = plan_direct_launch(p0, fmt, fmt == FMT_F32 ? OUT_F32 : OUT_U32,
-                                       vmax_for_nbits(nbits), part, &L);
+                                       vmax_for_nbits(nbits), part, &L, &tabs);
       if (r != DD_OK) return r;
+      if (hold) hold->insert(hold->end(), tabs.begin(), tabs.end());
       if ((r = run_launch(p0, L, st)) != DD_OK) return r;
       k0 = k1;
     }
@@ -331,6 +337,12 @@ dd_status dd_batch_launch(dd_batch b, void* cuda_stream, int64_t* nsamps_out) {
   return DD_OK;
 }
 
+extern "C" {
+
+dd_status dd_batch_launch(dd_batch b, void* cuda_stream, int64_t* nsamps_out) {
+  return batch_launch(b, cuda_stream, nsamps_out, nullptr);
+}
+
 // Graph capture of a batch launch (steady-state streaming).  The capture
 // runs dd_batch_launch's host logic on a capturing stream, so every copy,
 // memset and kernel it issues becomes a graph node; the streams' host state
@@ -340,6 +352,9 @@ struct dd_batch_graph_s {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   int cur0 = 0;                   // first stream's tail buffer when variant 0 was taken
   std::vector<int64_t> nouts;     // outputs per add (the same on every replay)
+  // staging tables the captured kernels read: held here, so that no later
+  // execute, autotune or query on the plans can free them under the graph
+  std::vector<std::shared_ptr<StageTab>> tabs;
   ~dd_batch_graph_s() {
     for (auto& e : exec)
       if (e) cudaGraphExecDestroy(e);
@@ -383,7 +398,7 @@ dd_status dd_batch_graph_create(dd_batch_graph* out, dd_batch b) {
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      result = dd_batch_launch(b, cs, g->nouts.data());
+      result = batch_launch(b, cs, g->nouts.data(), &g->tabs);
       e = cudaStreamEndCapture(cs, &graph);
       if (e == cudaSuccess && result == DD_OK)
         e = cudaGraphInstantiate(&g->exec[v], graph, 0);

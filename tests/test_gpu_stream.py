@@ -123,9 +123,14 @@ def test_batch_equals_individual_streams(orc):
         assert np.array_equal(gb, orc.direct(xs[i], 8, p.nchans, nout, odelays(orc, p)))
 
 
-def test_batch_graph_replay_equals_the_oracle(orc):
+@pytest.mark.parametrize("churn", [False, True])
+def test_batch_graph_replay_equals_the_oracle(orc, churn):
     """A captured batch launch replayed gulp after gulp (new data written
-    into the same input buffers) continues every beam's series exactly."""
+    into the same input buffers) continues every beam's series exactly.
+    With churn, each plan's staging-table cache is refilled past its bound
+    (executes under 17 other tilings, then the tiling is put back) between
+    capture and replay: the graph holds the tables its kernels read, so the
+    replay still reads live tables."""
     torch = torch_cuda()
     plans = [_plan(256, 40, 400.0), _plan(128, 23, 300.0), _plan(256, 17, 250.0)]
     G = 2048
@@ -152,6 +157,17 @@ def test_batch_graph_replay_equals_the_oracle(orc):
         load(k)
         collect(batch.launch())
     graph = batch.capture()
+    if churn:
+        for p in plans:
+            tilings = [(b, cc, kk) for (b, kk) in ((32, 4), (64, 2), (16, 4), (32, 2), (32, 8))
+                       for cc in (4, 8, 16)] + [(32, 32, 4), (64, 32, 2)]
+            x = torch.zeros((G + p.max_delay, p.nchans // 4), dtype=torch.uint8, device="cuda")
+            o = torch.zeros((p.dm_count, G), dtype=torch.int32, device="cuda")
+            for t in tilings:
+                p.set_tuning(*t)
+                p.execute(x, 2, G, o)
+            p.set_tuning(32, 32, -1)   # the tiling the graph was captured with
+        torch.cuda.synchronize()
     for k in range(2, ngulps):
         load(k)
         collect(graph.launch())

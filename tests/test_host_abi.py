@@ -213,3 +213,22 @@ def test_chunk_geometry_8bit_wide_trials():
     assert g["chans_per_chunk"][0] == 32 and g["chans_per_chunk"][-1] == 4
     with pytest.raises(dd.DedispError):
         p.chunk_geometry(3)
+
+
+def test_noalloc_rejects_bad_arguments_before_any_device_work():
+    """dd_execute_noalloc validates on the host before it looks up its
+    scratch: none of these reach the device (this runs without a GPU)."""
+    lib = dd.lib()
+    plan = dd.Plan(64, 64e-6, 1500.0, -1.0, dms=[0.0, 10.0])
+    h = plan.handle
+    buf = ctypes.c_void_p(16)  # never dereferenced: every call below is rejected first
+    ok_stride = 64
+    assert lib.dd_execute_noalloc(None, 100, buf, 8, ok_stride, buf, 100, None) == 1
+    assert lib.dd_execute_noalloc(h, 100, None, 8, ok_stride, buf, 100, None) == 1
+    assert lib.dd_execute_noalloc(h, 100, buf, 8, ok_stride, None, 100, None) == 1
+    assert lib.dd_execute_noalloc(h, 0, buf, 8, ok_stride, buf, 100, None) == 1
+    assert lib.dd_execute_noalloc(h, 100, buf, 8, ok_stride, buf, 99, None) == 1
+    assert lib.dd_execute_noalloc(h, 100, buf, 3, ok_stride, buf, 100, None) == 3
+    assert lib.dd_execute_noalloc(h, 100, buf, 8, ok_stride - 1, buf, 100, None) == 1
+    plan.set_output_bits(8)   # scaled output: the call writes uint32 rows only
+    assert lib.dd_execute_noalloc(h, 100, buf, 8, ok_stride, buf, 100, None) == 1

@@ -78,3 +78,47 @@ def test_noalloc_rejects_problems_beyond_the_scratch():
     assert rc == 5          # DD_ERR_OOM: rejected before anything is launched
     torch.cuda.synchronize()
     assert int(out.min()) == 7 and int(out.max()) == 7
+
+
+def _oracle_direct(plan, x, nbits, nsamps):
+    import oracle
+    oracle.build()
+    d = oracle.delay_table(plan.nchans, plan.f0, plan.df, plan.dt, plan.dms)
+    return oracle.direct(x, nbits, plan.nchans, nsamps, d)
+
+
+def test_noalloc_equals_the_oracle_and_allocates_nothing():
+    """Against the oracle's Eq. 2 directly, on two calls in a row; and the
+    device's free memory is unchanged across the calls, also when the plan's
+    staging-table cache is full and the call needs a table it does not hold
+    (the call then builds it on the host alone and frees nothing)."""
+    torch = torch_cuda()
+    c = configs.SURVEY
+    full = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
+    plan = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dms=full.dms[::9])
+    nsamps = 2500
+    rows = nsamps + plan.max_delay
+    xs = [synth.uniform_packed(s, 0, rows, 1024, 2) for s in (71, 72)]
+    refs = [_oracle_direct(plan, x, 2, nsamps) for x in xs]
+    d_ins = [torch.from_numpy(x).cuda() for x in xs]
+    outs = [torch.full((plan.dm_count, nsamps), -3, dtype=torch.int32, device="cuda")
+            for _ in range(3)]
+    # fill the plan's table cache (16 entries) with uploaded tables of other
+    # tilings; the no-alloc calls then use a 17th
+    fill = [(b, cc, k) for (b, k) in ((32, 4), (64, 2), (16, 4), (32, 2), (32, 8))
+            for cc in (8, 16, 32)] + [(32, 4, 4)]
+    assert len(fill) == 16
+    for t in fill:
+        plan.set_tuning(*t)
+        plan.execute(d_ins[0], 2, nsamps, outs[2])
+    plan.set_tuning(64, 4, 2)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for k, (d_in, ref) in enumerate(zip(d_ins, refs)):
+        assert _call_noalloc(plan, d_in, 2, nsamps, outs[k], torch) == 0
+        torch.cuda.synchronize()
+        assert np.array_equal(outs[k].cpu().numpy().view(np.uint32), ref), k
+    assert _call_noalloc(plan, d_ins[0], 2, nsamps, outs[0], torch) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
