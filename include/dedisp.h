@@ -371,9 +371,30 @@ typedef struct {
  * max_inflight (1..8) launches queued on the GPU. */
 dd_status dd_server_create(dd_server *server, size_t arena_bytes, int max_batch,
                            int max_inflight);
-/* Waits for every launch in flight, then frees the server, its streams and
- * its arena (plans stay with the caller). */
+/* Waits for every launch in flight (without a deadline: the arena cannot
+ * be freed under running work; call dd_server_drain first to find out
+ * whether the GPU still answers), then frees the server, its streams and its
+ * arena (plans stay with the caller). */
 void dd_server_destroy(dd_server server);
+
+/* Deadline of the server's host waits, in milliseconds (0, the default: no
+ * deadline).  A wait that reaches it returns DD_ERR_TIMEOUT and leaves the
+ * launch in flight, where a later dd_server_step or dd_server_drain
+ * retires it once it ends: the server stays usable.  The deadline guards
+ * the host against a GPU or driver that stops answering; the kernels' own
+ * waits are bounded on the device. */
+dd_status dd_server_set_timeout(dd_server server, double timeout_ms);
+
+/* Wait for every launch in flight and retire it, within the server's
+ * deadline (DD_ERR_TIMEOUT when launches are still running at it). */
+dd_status dd_server_drain(dd_server server);
+
+/* Queue a pause of ms milliseconds (at most 60 s) on the compute stream
+ * before the transform of the next launch.  The pause is a host callback
+ * in the stream, with no device work: it makes a launch late on purpose, so
+ * that deadlines and the scheduler's handling of slow launches can be
+ * exercised without disturbing the GPU. */
+dd_status dd_server_pause_next_launch(dd_server server, double ms);
 
 /* Register a beam: its plan (band, DM list; must outlive the server), input
  * bits and largest gulp.  The beam keeps its overlap tail on the device. */
@@ -392,8 +413,9 @@ dd_status dd_server_submit(dd_server server, int beam, const void *in_host, int6
 
 /* One scheduling pass: retire launches that finished, admit queued gulps
  * and launch them.  With wait != 0 and nothing admissible it first waits
- * for the oldest launch in flight.  *admitted (may be null) receives the
- * gulps launched by this pass. */
+ * for the oldest launch in flight, at most the server's deadline
+ * (DD_ERR_TIMEOUT if it is still running then).  *admitted (may be null)
+ * receives the gulps launched by this pass. */
 dd_status dd_server_step(dd_server server, int wait, int *admitted);
 
 /* Up to max completed requests, oldest first; *n receives the count. */

@@ -72,6 +72,9 @@ def _load_lib():
         "dd_plan_reset_kernel_timing": (I, [P]),
         "dd_execute": (I, [P, I64, P, I, I64, P, I64, P, ctypes.c_uint]),
         "dd_execute_noalloc": (I, [P, I64, P, I, I64, P, I64, P]),
+        "dd_server_set_timeout": (I, [P, D]),
+        "dd_server_drain": (I, [P]),
+        "dd_server_pause_next_launch": (I, [P, D]),
         "dd_stream_create": (I, [pp(P), P, I, I64]),
         "dd_stream_destroy": (None, [P]),
         "dd_stream_push": (I, [P, P, I64, I64, P, I64, pp(I64), P, ctypes.c_uint]),
@@ -524,6 +527,19 @@ class Server:
         n = ctypes.c_int()
         _check(_lib.dd_server_step(self._h, 1 if wait else 0, ctypes.byref(n)), "dd_server_step")
         return n.value
+
+    def set_timeout(self, timeout_ms):
+        """Deadline of host waits (0: none); a wait past it raises code 7."""
+        _check(_lib.dd_server_set_timeout(self._h, float(timeout_ms)), "dd_server_set_timeout")
+
+    def drain(self):
+        """Wait (within the deadline) for every launch in flight."""
+        _check(_lib.dd_server_drain(self._h), "dd_server_drain")
+
+    def pause_next_launch(self, ms):
+        """Delay the next launch's transform by a host-side pause of ms."""
+        _check(_lib.dd_server_pause_next_launch(self._h, float(ms)),
+               "dd_server_pause_next_launch")
 
     def poll(self, max_n=256):
         arr = (RequestInfo * max_n)()

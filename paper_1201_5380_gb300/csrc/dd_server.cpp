@@ -125,6 +125,7 @@ struct Request {
 
 struct Launch {
   std::vector<uint64_t> reqs;
+  double pause_ms = 0.0;                // host-side pause queued before the transform
   cudaEvent_t done = nullptr;           // after everything of the launch
   std::atomic<int64_t> t_compute{0};    // stamped behind the transform
   std::atomic<int64_t> t_copied{0};     // stamped behind the output copies
@@ -132,6 +133,27 @@ struct Launch {
 
 void CUDART_CB stamp(void* slot) {
   static_cast<std::atomic<int64_t>*>(slot)->store(now_ns());
+}
+
+// A pause of the compute stream on the host (dd_server_pause_next_launch):
+// the stream waits for this callback; no device work is involved.
+void CUDART_CB pause_host(void* ms) {
+  std::this_thread::sleep_for(
+      std::chrono::microseconds((int64_t)(*static_cast<double*>(ms) * 1000.0)));
+}
+
+// Wait for an event, at most timeout_ms (<= 0: no limit).  The wait polls,
+// so a GPU that stops answering turns into DD_ERR_TIMEOUT on the host.
+dd_status wait_event(cudaEvent_t ev, double timeout_ms) {
+  if (timeout_ms <= 0.0) return cuda_status(cudaEventSynchronize(ev));
+  const int64_t deadline = now_ns() + (int64_t)(timeout_ms * 1e6);
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return DD_OK;
+    if (e != cudaErrorNotReady) return cuda_status(e);
+    if (now_ns() >= deadline) return DD_ERR_TIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
 }
 
 int64_t input_row_bytes(int nchans, int nbits) {
@@ -156,6 +178,8 @@ struct dd_server_s {
   std::deque<std::unique_ptr<Launch>> inflight;  // launch order
   std::deque<uint64_t> completed;               // not yet polled
   uint64_t next_id = 1;
+  double timeout_ms = 0.0;    // deadline of host waits (<= 0: none)
+  double pause_next_ms = 0.0; // dd_server_pause_next_launch
 
   ~dd_server_s() {
     for (auto& l : inflight)
@@ -179,12 +203,16 @@ struct dd_server_s {
     }
   }
 
-  // Retire launches whose work has finished (in launch order).
-  void retire(bool wait_front) {
+  // Retire launches whose work has finished (in launch order).  With
+  // wait_front, first wait for the oldest launch (at most timeout_ms); a
+  // launch still running at the deadline stays in flight and DD_ERR_TIMEOUT
+  // is returned.
+  dd_status retire(bool wait_front) {
     while (!inflight.empty()) {
       Launch& l = *inflight.front();
       if (wait_front) {
-        cudaEventSynchronize(l.done);
+        const dd_status w = wait_event(l.done, timeout_ms);
+        if (w != DD_OK) return w;
         wait_front = false;
       } else if (cudaEventQuery(l.done) != cudaSuccess) {
         break;
@@ -199,6 +227,7 @@ struct dd_server_s {
       cudaEventDestroy(l.done);
       inflight.pop_front();
     }
+    return DD_OK;
   }
 
   // Fail a launch that could not be issued: its requests complete with `st`.
@@ -277,6 +306,16 @@ struct dd_server_s {
       *err = cuda_status(e);
       fail(take, *err);
       return 0;
+    }
+    if (pause_next_ms > 0.0) {
+      L->pause_ms = pause_next_ms;
+      pause_next_ms = 0.0;
+      e = cudaLaunchHostFunc(comp, pause_host, &L->pause_ms);
+      if (e != cudaSuccess) {
+        *err = cuda_status(e);
+        fail(take, *err);
+        return 0;
+      }
     }
     // one batched launch over every admitted beam
     dd_batch_clear(batch);
@@ -418,11 +457,40 @@ dd_status dd_server_step(dd_server s, int wait, int* admitted) {
   dd_status err = DD_OK;
   int n = s->admit_and_launch(&err);
   if (n == 0 && err == DD_OK && wait && !s->inflight.empty()) {
-    s->retire(true);
-    n = s->admit_and_launch(&err);
+    err = s->retire(true);
+    if (err == DD_OK) n = s->admit_and_launch(&err);
   }
   if (admitted) *admitted = n;
   return err;
+}
+
+dd_status dd_server_set_timeout(dd_server s, double timeout_ms) {
+  if (!s || !(timeout_ms >= 0.0)) return DD_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->timeout_ms = timeout_ms;
+  return DD_OK;
+}
+
+dd_status dd_server_drain(dd_server s) {
+  if (!s) return DD_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  cudaSetDevice(s->device);
+  const int64_t deadline = now_ns() + (int64_t)(s->timeout_ms * 1e6);
+  while (!s->inflight.empty()) {
+    const double left = s->timeout_ms > 0.0 ? (double)(deadline - now_ns()) / 1e6 : 0.0;
+    if (s->timeout_ms > 0.0 && left <= 0.0) return DD_ERR_TIMEOUT;
+    const dd_status w = wait_event(s->inflight.front()->done, left);
+    if (w != DD_OK) return w;
+    s->retire(false);
+  }
+  return DD_OK;
+}
+
+dd_status dd_server_pause_next_launch(dd_server s, double ms) {
+  if (!s || !(ms >= 0.0) || ms > 60000.0) return DD_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->pause_next_ms = ms;
+  return DD_OK;
 }
 
 dd_status dd_server_poll(dd_server s, dd_request_info* out, int max, int* n) {

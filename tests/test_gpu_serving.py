@@ -150,3 +150,54 @@ def test_server_rejects_a_gulp_larger_than_the_arena():
     with pytest.raises(dd.DedispError) as e:
         server.submit(b, x)
     assert e.value.code == 11
+
+
+def test_server_wait_deadline_returns_timeout_and_recovers(orc):
+    """A launch held back on the host (a 700 ms pause in the compute stream,
+    no device work) makes a waiting step reach the server's 100 ms deadline:
+    DD_ERR_TIMEOUT (7) comes back, the launch stays in flight, and once the
+    pause ends the server retires it and every result is still exact."""
+    import time
+    torch_cuda()
+    plans = _beam_plans(2)
+    sizes = [[1500, 1300], [1100, 1700]]
+    xs = _series(plans, sizes)
+    server = dd.Server(arena_bytes=64 << 20, max_batch=2, max_inflight=2)
+    beams = {b: server.add_beam(p, 8, 1700) for b, p in enumerate(plans)}
+    server.set_timeout(100.0)
+    server.pause_next_launch(700.0)
+    outs = {}
+    for b in beams:
+        o = np.zeros((plans[b].dm_count, sizes[b][0]), np.uint32)
+        outs[server.submit(beams[b], np.ascontiguousarray(xs[b][:sizes[b][0]]), None, o)] = (b, 0, o)
+    assert server.step() == 2          # both gulps in one launch, behind the pause
+    t0 = time.monotonic()
+    with pytest.raises(dd.DedispError) as e:
+        server.step(wait=True)
+    waited = time.monotonic() - t0
+    assert e.value.code == 7
+    assert 0.05 < waited < 0.6
+    assert server.stats()["inflight"] == 2
+    with pytest.raises(dd.DedispError) as e:
+        server.drain()                 # still inside the pause
+    assert e.value.code == 7
+    server.set_timeout(5000.0)
+    server.drain()
+    assert server.stats()["inflight"] == 0
+    for b in beams:                     # the server goes on serving
+        o = np.zeros((plans[b].dm_count, sizes[b][1]), np.uint32)
+        pos = sizes[b][0]
+        chunk = np.ascontiguousarray(xs[b][pos:pos + sizes[b][1]])
+        outs[server.submit(beams[b], chunk, None, o)] = (b, 1, o)
+    server.step()
+    server.drain()
+    done = {i["request"]: i for i in server.poll()}
+    assert len(done) == 4
+    per = {b: {} for b in beams}
+    for r, (b, k, o) in outs.items():
+        assert done[r]["status"] == 0
+        per[b][k] = o[:, :done[r]["nsamps_out"]]
+    for b, p in enumerate(plans):
+        got = np.concatenate([per[b][0], per[b][1]], axis=1)
+        assert np.array_equal(got, _expected(orc, p, xs[b], 8)), b
+    server.close()
