@@ -89,6 +89,15 @@ def _load():
             "orc_subband_smear_taylor": (f64, [f64, f64, ctypes.c_int,
                                                ctypes.c_int, f64]),
             "orc_relative_smearing": (f64, [f64, f64]),
+            "orc_tree_theta": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+            "orc_tree_phi": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+            "orc_tree": (ctypes.c_int, [P, ctypes.c_int, i64, P]),
+            "orc_tree_max_delay": (i64, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+            "orc_tree_piecewise_u32": (ctypes.c_int, [P, ctypes.c_int, i64, ctypes.c_int,
+                                                      ctypes.c_int, i64, P, ctypes.c_int,
+                                                      P, P, i64]),
+            "orc_tree_dm_limit": (f64, [f64, f64, f64, ctypes.c_int, ctypes.c_int]),
+            "orc_tree_smear_bound": (f64, [f64, f64, f64, ctypes.c_int, ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -346,3 +355,69 @@ def subband_smear_taylor(f0, df, nchans, chans_per_sb, dm_nom_step) -> float:
 def relative_smearing(w_s, t_sb_s) -> float:
     """mu_SB of Eq. (eq:RelativeSmearingSubband)."""
     return float(_load().orc_relative_smearing(w_s, t_sb_s))
+
+
+# ---------------------------------------------------------------------------
+# Tree dedispersion (Sec. 3.1) and the piecewise linear tree (Sec. 3.1.1)
+# ---------------------------------------------------------------------------
+
+def tree_theta(i, nu) -> int:
+    """Eq. (tree_integer_delay)."""
+    return int(_load().orc_tree_theta(int(i), int(nu)))
+
+
+def tree_phi(r, nu) -> int:
+    """Eq. (shuffle) at radix r = 2^i."""
+    return int(_load().orc_tree_phi(int(r), int(nu)))
+
+
+def tree(rows) -> np.ndarray:
+    """The basic tree (Eq. tree_algorithm_first .. last) on N = 2^m rows of
+    L samples: returns N rows (trail d' = 0 .. N-1) of L - (N - 1) samples."""
+    a = np.ascontiguousarray(rows, dtype=np.int64)
+    n, L = a.shape
+    out = np.zeros((n, L - (n - 1)), np.int64)
+    rc = _load().orc_tree(_ptr(a), n, L, _ptr(out))
+    if rc:
+        raise ValueError("orc_tree: bad arguments (%d)" % rc)
+    return out
+
+
+def delay_table_ext(nchans, f0, df, dt, dms) -> np.ndarray:
+    """Eq. 4 at channels 0 .. N_nu (one column past the band: the edge
+    nu_{N_s} that the last sub-band's linear DM reaches)."""
+    return delay_table(nchans + 1, f0, df, dt, dms)
+
+
+def tree_max_delay(dext, nchans, nsub) -> int:
+    """Input rows beyond the gulp that the piecewise linear tree reads."""
+    d = np.ascontiguousarray(dext, dtype=np.int32)
+    v = int(_load().orc_tree_max_delay(_ptr(d), d.shape[0], nchans, nsub))
+    if v < 0:
+        raise ValueError("a trial lies beyond the piecewise diagonal DM")
+    return v
+
+
+def tree_piecewise(packed, nbits, nchans, nsub, nsamps, dext, mask=None) -> np.ndarray:
+    """The piecewise linear tree method (Sec. 3.1.1): the basic tree on each
+    sub-band of nsub channels (stage 1), then Eq. (combining_subbands)."""
+    x = np.ascontiguousarray(packed, dtype=np.uint8)
+    d = np.ascontiguousarray(dext, dtype=np.int32)
+    ndm = d.shape[0]
+    out = np.zeros((ndm, nsamps), np.uint32)
+    m = _mask_arr(mask, nchans)
+    rc = _load().orc_tree_piecewise_u32(_ptr(x), nbits, x.strides[0], nchans, nsub, nsamps,
+                                        _ptr(d), ndm, _ptr(m), _ptr(out), nsamps)
+    if rc:
+        raise ValueError("orc_tree_piecewise_u32 failed (%d)" % rc)
+    return out
+
+
+def tree_dm_limit(f0, df, dt, nchans, nsub) -> float:
+    """Eq. (tree_dm_limit): the piecewise diagonal DM."""
+    return float(_load().orc_tree_dm_limit(f0, df, dt, nchans, nsub))
+
+
+def tree_smear_bound(dm, f0, df, nchans, nsub) -> float:
+    """App. A, Eq. (subband_error), seconds."""
+    return float(_load().orc_tree_smear_bound(dm, f0, df, nchans, nsub))

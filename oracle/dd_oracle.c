@@ -19,6 +19,12 @@
  *     the sub-band's first channel);
  *   - the sub-band smearing bound of Appendix B (eq:subband_smear_approx,
  *     eq:RelativeSmearingSubband);
+ *   - tree dedispersion, Sec. 3.1 (Eq. tree_algorithm_first .. last with the
+ *     delay Theta of Eq. tree_integer_delay and the shuffle Phi of Eq.
+ *     shuffle, step by step), and the piecewise linear tree method of Sec.
+ *     3.1.1 (the tree per sub-band, Eq. subband_result, then Eq.
+ *     combining_subbands), with its DM limit (Eq. tree_dm_limit) and the
+ *     smear bound of Appendix A (Eq. subband_error);
  *   - the trial-DM list: the paper only says it bounds the smearing due to
  *     a wrong trial DM (Sec. 5.2, after Cordes & McLaughlin 2003); the
  *     recurrence below is this project's reading of that rule (see
@@ -424,4 +430,183 @@ double orc_subband_smear_taylor(double f0_mhz, double df_mhz, int nchans,
 double orc_relative_smearing(double w_s, double t_sb_s)
 {
     return sqrt(w_s * w_s + t_sb_s * t_sb_s) / w_s;
+}
+
+/* ---------------------------------------------------------------------------
+ * Tree dedispersion (Sec. 3.1) and the piecewise linear tree method
+ * (Sec. 3.1.1).
+ *
+ * The basic tree computes D'[d'][t] = sum_nu A[nu][t + dt'(d', nu)] for the
+ * linear trails d' = 0 .. N-1 of a block of N = 2^m channels in m steps:
+ *   A^{i+1}[2nu  ][t] = A^i[Phi(i, 2nu)][t] + A^i[Phi(i, 2nu+1)][t + Theta(i, 2nu)]
+ *   A^{i+1}[2nu+1][t] = A^i[Phi(i, 2nu)][t] + A^i[Phi(i, 2nu+1)][t + Theta(i, 2nu+1)]
+ * with the integer delay Theta of Eq. (tree_integer_delay) and the shuffle
+ * Phi of Eq. (shuffle) at radix r = 2^i, all divisions truncated; after the
+ * last step row d' holds D'[d'].  The delays it applies are the tree's own
+ * approximation of the rounded linear trail of Eq. (tree); they coincide with
+ * round(d' nu / (N - 1)) only for small blocks.
+ *
+ * Each step reads A^i at t + Theta <= t + r, so its output is r samples
+ * shorter than its input: from L input samples the tree returns L - (N - 1).
+ * ------------------------------------------------------------------------- */
+
+/* Eq. (tree_integer_delay): Theta(i, nu) = [(nu mod 2^{i+1}) + 1] / 2. */
+int orc_tree_theta(int i, int nu)
+{
+    return ((nu % (2 << i)) + 1) / 2;
+}
+
+/* Eq. (shuffle): Phi(r, nu) = (nu mod 2) r + nu/2 + (nu/(2r)) r, r = 2^i. */
+int orc_tree_phi(int r, int nu)
+{
+    return (nu % 2) * r + nu / 2 + (nu / (2 * r)) * r;
+}
+
+static int orc_is_pow2(int n)
+{
+    return n > 0 && (n & (n - 1)) == 0;
+}
+
+/* The basic tree on n rows (a power of two) of len samples each, a[nu*len +
+ * t]; out receives n rows of len - (n - 1) samples, out[d'*(len-n+1) + t].
+ * Returns 0, or -1 on a bad argument. */
+int orc_tree(const int64_t *a, int n, int64_t len, int64_t *out)
+{
+    if (!orc_is_pow2(n) || len < n) return -1;
+    int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * (size_t)n * (size_t)len);
+    int64_t *nxt = (int64_t *)malloc(sizeof(int64_t) * (size_t)n * (size_t)len);
+    if (!cur || !nxt) { free(cur); free(nxt); return -1; }
+    memcpy(cur, a, sizeof(int64_t) * (size_t)n * (size_t)len);
+    int64_t lcur = len;
+    for (int i = 0; (1 << i) < n; ++i) {
+        int r = 1 << i;
+        int64_t lnext = lcur - r;
+        for (int v = 0; v < n / 2; ++v) {
+            const int64_t *lo = cur + (int64_t)orc_tree_phi(r, 2 * v) * len;
+            const int64_t *hi = cur + (int64_t)orc_tree_phi(r, 2 * v + 1) * len;
+            for (int j = 0; j < 2; ++j) {
+                int th = orc_tree_theta(i, 2 * v + j);
+                int64_t *o = nxt + (int64_t)(2 * v + j) * len;
+                for (int64_t t = 0; t < lnext; ++t) o[t] = lo[t] + hi[t + th];
+            }
+        }
+        int64_t *sw = cur; cur = nxt; nxt = sw;
+        lcur = lnext;
+    }
+    for (int d = 0; d < n; ++d)
+        memcpy(out + (int64_t)d * lcur, cur + (int64_t)d * len, sizeof(int64_t) * (size_t)lcur);
+    free(cur);
+    free(nxt);
+    return 0;
+}
+
+/* Stage-2 quantities of the piecewise linear tree (Sec. 3.1.1) for trial d
+ * and sub-band n, from a delay table of nchans + 1 columns (Eq. 4 evaluated
+ * at channels 0 .. N_nu, the last one being the band edge nu_{N_s}):
+ *   d'_n(d)   = dt(d, nu_{n+1}) - dt(d, nu_n)      (the sub-band's linear DM,
+ *               read as the difference of the rounded delays, the first form
+ *               the paper prints),
+ *   dt''_n(d) = dt(d, nu_n)                        (Eq. combining_subbands:
+ *               the sum over m < n of the per-sub-band increments telescopes).
+ * Returns -3 if d'_n(d) falls outside 0 .. N'-1 (the trial lies beyond the
+ * piecewise diagonal DM of Eq. tree_dm_limit). */
+static int orc_tree_stage2_terms(const int32_t *dext, int nchans, int nsub, int d, int n,
+                                 int32_t *dprime, int32_t *shift)
+{
+    const int32_t *row = dext + (int64_t)d * (nchans + 1);
+    int32_t a = row[(int64_t)n * nsub], b = row[(int64_t)(n + 1) * nsub];
+    *dprime = b - a;
+    *shift = a;
+    return (*dprime < 0 || *dprime >= nsub) ? -3 : 0;
+}
+
+/* Input rows beyond nsamps that the piecewise linear tree reads:
+ * max_{d,n} dt''_n(d) + (N' - 1).  -3 as above. */
+int64_t orc_tree_max_delay(const int32_t *dext, int ndm, int nchans, int nsub)
+{
+    int32_t m = 0;
+    for (int d = 0; d < ndm; ++d)
+        for (int n = 0; n < nchans / nsub; ++n) {
+            int32_t dp, sh;
+            if (orc_tree_stage2_terms(dext, nchans, nsub, d, n, &dp, &sh)) return -3;
+            if (sh > m) m = sh;
+        }
+    return (int64_t)m + nsub - 1;
+}
+
+/* The piecewise linear tree method, integer input.
+ * Stage 1 (Eq. subband_result): the basic tree on each sub-band of N' = nsub
+ *   channels, S[n][d'][t] = sum_{nu'} A[nu_n + nu'][t + tree delay(d', nu')],
+ *   for t < nsamps + max dt''.
+ * Stage 2 (Eq. combining_subbands):
+ *   D[d][t] = sum_n S[n][d'_n(d)][t + dt''_n(d)].
+ * dext is the (ndm) x (nchans + 1) delay table described above.  The input
+ * must hold nsamps + orc_tree_max_delay rows.  Returns 0, -1 on a bad
+ * argument, -2 if a sum does not fit 32 bits, -3 for a trial beyond the
+ * piecewise diagonal DM. */
+int orc_tree_piecewise_u32(const uint8_t *in, int nbits, int64_t row_stride, int nchans,
+                           int nsub, int64_t nsamps, const int32_t *dext, int ndm,
+                           const uint8_t *mask, uint32_t *out, int64_t out_stride)
+{
+    if (!orc_nbits_ok(nbits) || !orc_is_pow2(nsub) || nchans % nsub != 0 || nsamps <= 0 ||
+        ndm <= 0)
+        return -1;
+    int64_t extra = orc_tree_max_delay(dext, ndm, nchans, nsub);
+    if (extra < 0) return (int)extra;
+    int nsb = nchans / nsub;
+    int64_t len_in = nsamps + extra;             /* input rows read */
+    int64_t len1 = len_in - (nsub - 1);          /* stage-1 samples per row */
+    int64_t *S = (int64_t *)malloc(sizeof(int64_t) * (size_t)nchans * (size_t)len1);
+    if (!S) return -1;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int n = 0; n < nsb; ++n) {
+        int64_t *a = (int64_t *)malloc(sizeof(int64_t) * (size_t)nsub * (size_t)len_in);
+        if (!a) { bad = 1; continue; }
+        for (int v = 0; v < nsub; ++v) {
+            int c = n * nsub + v;
+            int64_t m = mask ? mask[c] : 1;
+            for (int64_t t = 0; t < len_in; ++t)
+                a[(int64_t)v * len_in + t] = m * (int64_t)orc_sample(in, nbits, row_stride, c, t);
+        }
+        if (orc_tree(a, nsub, len_in, S + (int64_t)n * nsub * len1)) bad = 1;
+        free(a);
+    }
+    if (bad) { free(S); return -1; }
+    int overflow = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : overflow)
+    for (int d = 0; d < ndm; ++d) {
+        for (int64_t t = 0; t < nsamps; ++t) {
+            int64_t acc = 0;
+            for (int n = 0; n < nsb; ++n) {
+                int32_t dp, sh;
+                orc_tree_stage2_terms(dext, nchans, nsub, d, n, &dp, &sh);
+                acc += S[((int64_t)n * nsub + dp) * len1 + t + sh];
+            }
+            if (acc < 0 || acc > 0xFFFFFFFFll) overflow = 1;
+            out[(int64_t)d * out_stride + t] = (uint32_t)acc;
+        }
+    }
+    free(S);
+    return overflow ? -2 : 0;
+}
+
+/* Eq. (tree_dm_limit): the piecewise diagonal DM,
+ * (N' - 1/2) / (Delta T(N_nu) - Delta T(N_nu - N')). */
+double orc_tree_dm_limit(double f0_mhz, double df_mhz, double dt_s, int nchans, int nsub)
+{
+    double hi = orc_partial_delay(f0_mhz, df_mhz, dt_s, nchans);
+    double lo = orc_partial_delay(f0_mhz, df_mhz, dt_s, nchans - nsub);
+    return ((double)nsub - 0.5) / (hi - lo);
+}
+
+/* Appendix A, Eq. (subband_error): the piecewise linear approximation's
+ * smear, t_tree <= (3/4) DM (k_DM / nu0^2) (N'/N_nu)^2 lambda^2 / (1 + lambda)^4,
+ * lambda = dnu N_nu / nu0.  Seconds. */
+double orc_tree_smear_bound(double dm, double f0_mhz, double df_mhz, int nchans, int nsub)
+{
+    double lam = df_mhz * (double)nchans / f0_mhz;
+    double r = (double)nsub / (double)nchans;
+    double q = (1.0 + lam) * (1.0 + lam);
+    return 0.75 * dm * (ORC_K_DM / (f0_mhz * f0_mhz)) * r * r * lam * lam / (q * q);
 }

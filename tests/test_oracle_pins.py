@@ -452,3 +452,202 @@ def test_scaled_output_keeps_the_top_bits(orc):
     assert orc.scale_output(s, 1024, 3, 8).dtype == np.uint8
     # 64 channels of 8-bit samples reach 16320 (14 bits): shift 6 for 8-bit
     assert orc.scale_output(np.array([16320, 63, 64]), 64, 255, 8).tolist() == [255, 0, 1]
+
+
+# ---------------------------------------------------------------------------
+# Tree dedispersion (Sec. 3.1) and the piecewise linear tree (Sec. 3.1.1)
+# ---------------------------------------------------------------------------
+
+def _tree_closed_form_delay(k, nu, n):
+    """Delay the tree applies to channel nu of trail k in a block of n = 2^m
+    channels, from the merge the tree performs at every level rather than
+    from its shuffle tables: a block of 2r channels takes trail k/2 in both
+    halves and shifts the upper half by (k + 1) / 2, so bit b of nu
+    contributes the shift of the level that merges blocks of 2^(b+1)
+    channels, ((k >> (m-1-b)) + 1) >> 1."""
+    m = n.bit_length() - 1
+    return sum(((k >> (m - 1 - b)) + 1) >> 1 for b in range(m) if (nu >> b) & 1)
+
+
+def _tree_impulse_delays(orc, n):
+    """The delay of every (trail, channel) measured on the oracle's tree: an
+    impulse in one channel comes out of trail k once, shifted by its delay."""
+    L = 3 * n + 8
+    tau = 2 * n + 4
+    out = np.zeros((n, n), np.int64)
+    for nu in range(n):
+        a = np.zeros((n, L), np.int64)
+        a[nu, tau] = 1
+        d = orc.tree(a)
+        assert d.shape == (n, L - (n - 1))
+        for k in range(n):
+            ts = np.flatnonzero(d[k])
+            assert ts.size == 1 and d[k, ts[0]] == 1   # every channel summed exactly once
+            out[k, nu] = tau - ts[0]
+    return out
+
+
+def test_tree_theta_and_shuffle_small_values(orc):
+    # Eq. (tree_integer_delay) and Eq. (shuffle) by hand: at step 0 the
+    # pairs are neighbouring channels, shifted by 0 and 1 sample; at step 1
+    # (radix 2) the pairs are rows (0, 2) and (1, 3) of each block of four
+    assert [orc.tree_theta(0, v) for v in range(4)] == [0, 1, 0, 1]
+    assert [orc.tree_theta(1, v) for v in range(8)] == [0, 1, 1, 2, 0, 1, 1, 2]
+    assert [orc.tree_phi(1, v) for v in range(4)] == [0, 1, 2, 3]
+    assert [orc.tree_phi(2, v) for v in range(8)] == [0, 2, 1, 3, 4, 6, 5, 7]
+    assert [orc.tree_phi(4, v) for v in range(8)] == [0, 4, 1, 5, 2, 6, 3, 7]
+
+
+@pytest.mark.parametrize("n", [2, 4, 8])
+def test_tree_small_blocks_equal_the_rounded_linear_trails(orc, n):
+    """For blocks of up to 8 channels the tree computes Eq. (tree) exactly:
+    D'[k][t] = sum_nu A[nu][t + round(k nu / (n - 1))] (brute force)."""
+    rng = np.random.default_rng(n)
+    L = 60
+    a = rng.integers(0, 256, (n, L)).astype(np.int64)
+    got = orc.tree(a)
+    Lo = L - (n - 1)
+    for k in range(n):
+        ref = np.zeros(Lo, np.int64)
+        for nu in range(n):
+            s = int(np.floor(Fraction(k * nu, n - 1) + Fraction(1, 2)))
+            ref += a[nu, s:s + Lo]
+        assert np.array_equal(got[k], ref), k
+
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 32, 64])
+def test_tree_delays_follow_the_merge_recursion(orc, n):
+    """Every channel of every trail is summed once, at the delay the merge
+    recursion gives; the trails run from delay 0 at channel 0 to exactly k at
+    channel n - 1 (Eq. tree), monotone, and within log2(n)/6 samples of the
+    straight line (under one sample up to 32 channels)."""
+    got = _tree_impulse_delays(orc, n)
+    cf = np.array([[_tree_closed_form_delay(k, v, n) for v in range(n)] for k in range(n)])
+    assert np.array_equal(got, cf)
+    k = np.arange(n)[:, None]
+    nu = np.arange(n)[None, :]
+    assert np.all(got[:, 0] == 0) and np.array_equal(got[:, -1], np.arange(n))
+    assert np.all(np.diff(got, axis=1) >= 0)
+    dev = np.abs(got - k * nu / max(n - 1, 1))
+    assert np.all(dev <= (n.bit_length() - 1) / 6.0 + 1e-12)
+    if n <= 32:
+        assert np.all(dev < 1.0)
+
+
+def test_tree_matches_brute_force_on_random_rows(orc):
+    rng = np.random.default_rng(3)
+    n, L = 32, 200
+    a = rng.integers(0, 4, (n, L)).astype(np.int64)
+    got = orc.tree(a)
+    Lo = L - (n - 1)
+    for k in range(n):
+        ref = sum(a[v, _tree_closed_form_delay(k, v, n):][:Lo] for v in range(n))
+        assert np.array_equal(got[k], ref)
+
+
+def _tree_band(nchans=64, df=-1.5625):
+    return dict(nchans=nchans, f0=1500.0, df=df, dt=64e-6)
+
+
+def _piecewise_brute(orc, x_samples, band, nsub, dms, nsamps):
+    """Eq. (combining_subbands) summed channel by channel with the delays the
+    merge recursion gives (no tree, no stage-1 rows)."""
+    dext = orc.delay_table_ext(band["nchans"], band["f0"], band["df"], band["dt"], dms)
+    out = np.zeros((len(dms), nsamps), np.int64)
+    for d in range(len(dms)):
+        for n in range(band["nchans"] // nsub):
+            dp = int(dext[d, (n + 1) * nsub] - dext[d, n * nsub])
+            sh = int(dext[d, n * nsub])
+            for v in range(nsub):
+                s = sh + _tree_closed_form_delay(dp, v, nsub)
+                out[d] += x_samples[s:s + nsamps, n * nsub + v]
+    return out.astype(np.uint32)
+
+
+@pytest.mark.parametrize("nsub,nbits", [(8, 2), (16, 8), (32, 4)])
+def test_tree_piecewise_matches_channelwise_brute_force(orc, nsub, nbits):
+    band = _tree_band()
+    lim = orc.tree_dm_limit(band["f0"], band["df"], band["dt"], band["nchans"], nsub)
+    dms = np.linspace(0.0, 0.95 * lim, 23)
+    dext = orc.delay_table_ext(band["nchans"], band["f0"], band["df"], band["dt"], dms)
+    nsamps = 300
+    rows = nsamps + orc.tree_max_delay(dext, band["nchans"], nsub)
+    s = synth.uniform_samples(21, nsub, rows, band["nchans"], nbits)
+    got = orc.tree_piecewise(synth.pack(s, nbits), nbits, band["nchans"], nsub, nsamps, dext)
+    assert np.array_equal(got, _piecewise_brute(orc, s, band, nsub, dms, nsamps))
+
+
+def test_tree_piecewise_dm0_is_channel_sum(orc):
+    band = _tree_band()
+    dext = orc.delay_table_ext(band["nchans"], band["f0"], band["df"], band["dt"], [0.0, 0.0])
+    nsamps = 200
+    rows = nsamps + orc.tree_max_delay(dext, band["nchans"], 16)
+    s = synth.uniform_samples(22, 0, rows, band["nchans"], 8)
+    got = orc.tree_piecewise(synth.pack(s, 8), 8, band["nchans"], 16, nsamps, dext)
+    assert np.array_equal(got[0], s[:nsamps].astype(np.uint32).sum(axis=1))
+    assert np.array_equal(got[1], got[0])
+
+
+def test_tree_piecewise_meets_the_direct_delays_at_sub_band_edges(orc):
+    """An impulse in the first channel of a sub-band comes out at exactly
+    the direct transform's delay (Eq. 4): the stage-2 shift of Eq.
+    (combining_subbands) telescopes to it.  Inside a sub-band the piecewise
+    trail stays within App. A's bound (plus the rounding of the tree and of
+    the two delays it joins) of the direct trail."""
+    band = _tree_band()
+    nsub = 16
+    nch = band["nchans"]
+    lim = orc.tree_dm_limit(band["f0"], band["df"], band["dt"], nch, nsub)
+    dms = np.linspace(0.0, 0.99 * lim, 9)
+    dext = orc.delay_table_ext(nch, band["f0"], band["df"], band["dt"], dms)
+    direct = orc.delay_table(nch, band["f0"], band["df"], band["dt"], dms)
+    extra = orc.tree_max_delay(dext, nch, nsub)
+    nsamps = 8
+    tau = extra + 2
+    rows = nsamps + extra + tau
+    for c in range(nch):
+        s = np.zeros((rows, nch), np.uint8)
+        s[tau, c] = 1
+        out = orc.tree_piecewise(synth.pack(s, 8), 8, nch, nsub, tau + 1, dext)
+        for d in range(len(dms)):
+            ts = np.flatnonzero(out[d])
+            assert ts.size == 1
+            eff = tau - ts[0]
+            if c % nsub == 0:
+                assert eff == direct[d, c]
+            bound = orc.tree_smear_bound(dms[d], band["f0"], band["df"], nch, nsub) / band["dt"]
+            assert abs(eff - direct[d, c]) <= bound + 2.0
+
+
+def test_tree_piecewise_rejects_trials_beyond_the_diagonal(orc):
+    band = _tree_band()
+    lim = orc.tree_dm_limit(band["f0"], band["df"], band["dt"], band["nchans"], 16)
+    dext = orc.delay_table_ext(band["nchans"], band["f0"], band["df"], band["dt"],
+                               [0.0, 1.2 * lim])
+    with pytest.raises(ValueError):
+        orc.tree_max_delay(dext, band["nchans"], 16)
+
+
+def test_tree_dm_limit_and_smear_bound_values(orc):
+    """Eq. (tree_dm_limit) on the survey band by hand (Delta T from Eq. 3),
+    and App. A's bound against the quantity it bounds: the largest distance,
+    in time, between the dispersion curve of Eq. 3 and its chord across a
+    sub-band, found numerically over every sub-band of the band.  The bound
+    takes the curve's second derivative at the band's low edge, so it holds
+    everywhere and is nearly reached in the lowest sub-band."""
+    c = configs.SURVEY
+    k = 4.148808e3
+    dT = lambda ch: (k / c["dt"]) * ((c["f0"] + ch * c["df"]) ** -2 - c["f0"] ** -2)
+    for nsub in (16, 32, 64):
+        ref = (nsub - 0.5) / (dT(1024) - dT(1024 - nsub))
+        assert orc.tree_dm_limit(c["f0"], c["df"], c["dt"], 1024, nsub) == pytest.approx(ref, rel=1e-12)
+        dm = 1000.0
+        worst = 0.0
+        v = np.arange(nsub + 1)
+        for n in range(1024 // nsub):
+            a, b = n * nsub, (n + 1) * nsub
+            curve = np.array([dT(a + x) for x in v])
+            chord = dT(a) + (dT(b) - dT(a)) * v / nsub
+            worst = max(worst, float(np.abs(curve - chord).max()) * dm * c["dt"])
+        bound = orc.tree_smear_bound(dm, c["f0"], c["df"], 1024, nsub)
+        assert 0.9 * bound <= worst <= bound
