@@ -80,6 +80,8 @@ typedef enum dd_status {
                                dd_plan_set_subband) instead of direct */
 #define DD_SCRUNCH 0x4u     /* direct with time-scrunching (needs
                                dd_plan_set_scrunch; device pointers) */
+#define DD_TREE 0x8u        /* the piecewise linear tree method (needs
+                               dd_plan_set_tree; integer input) */
 
 typedef struct dd_plan_s *dd_plan;
 typedef struct dd_stream_s *dd_stream;
@@ -137,6 +139,30 @@ dd_status dd_plan_set_subband(dd_plan plan, int chans_per_subband,
  * Nominal trials stay exact either way. */
 dd_status dd_plan_set_subband_alignment(dd_plan plan, int centred);
 
+/* Enable the piecewise linear tree method of Sec. 3.1.1 (execute with
+ * DD_TREE): chans_per_subband (N') a power of two from 2 to 128 dividing
+ * nchans; 0 disables it.  Stage 1 runs the tree of Sec. 3.1 (Eq.
+ * tree_algorithm_first .. last, Theta of Eq. tree_integer_delay, the
+ * shuffle Phi of Eq. shuffle) on every sub-band of N' channels, giving the
+ * linear trails d' = 0 .. N'-1 of Eq. subband_result; stage 2 combines them
+ * by Eq. combining_subbands:
+ *     D[d][t] = sum_n S[n][d'_n(d)][t + delay(d, nN')],
+ *     d'_n(d) = delay(d, (n+1)N') - delay(d, nN'),
+ * with delay(d, N_nu), one channel past the band, from Eq. 3-4 at the band
+ * edge (so the band edge f0 + nchans*df must be > 0).  Every trial must
+ * satisfy d'_n(d) < N' in every sub-band, i.e. lie below the piecewise
+ * diagonal DM of Eq. tree_dm_limit (dd_plan_get_tree_dm_limit); an execute
+ * with a trial beyond it returns DD_ERR_INVALID_ARG.  Integer input (1, 2, 4
+ * or 8 bits), uint32 output; the input holds nsamps_out + the rows that
+ * dd_plan_get_input_rows reports with DD_TREE (the largest stage-2 shift
+ * plus N' - 1, the tree's own reach).  Results are approximate by design:
+ * the trails are piecewise linear (App. A bounds the smear). */
+dd_status dd_plan_set_tree(dd_plan plan, int chans_per_subband);
+/* Eq. (tree_dm_limit): (N' - 1/2) / (Delta T(N_nu) - Delta T(N_nu - N')),
+ * the DM up to which the basic piecewise linear tree reaches, for
+ * N' = chans_per_subband. */
+dd_status dd_plan_get_tree_dm_limit(dd_plan plan, int chans_per_subband, double *dm_diag);
+
 /* Bits per output sample of dd_execute: 32 (exact uint32 sums, the
  * default), or 16 / 8 for the scaled low-bit output of Sec. 4.3.  The paper
  * gives no scaling rule; here a scaled sample is
@@ -159,7 +185,7 @@ dd_status dd_plan_set_scrunch(dd_plan plan, int max_factor);
 /* Factor of every trial (1 when scrunching is off). */
 dd_status dd_plan_get_scrunch_factors(dd_plan plan, int32_t *factors);
 /* Input rows an execute of nsamps_out samples reads with these flags
- * (DD_SUBBAND / DD_SCRUNCH): nsamps_out + max_delay for direct. */
+ * (DD_SUBBAND / DD_SCRUNCH / DD_TREE): nsamps_out + max_delay for direct. */
 dd_status dd_plan_get_input_rows(dd_plan plan, int64_t nsamps_out, unsigned flags,
                                  int64_t *rows);
 

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libgb300dd.so")
 DD_DEVICE_PTRS = 0x1
 DD_SUBBAND = 0x2
 DD_SCRUNCH = 0x4
+DD_TREE = 0x8
 DD_IN_F32 = 32
 
 STATUS = {
@@ -72,6 +73,8 @@ def _load_lib():
         "dd_plan_reset_kernel_timing": (I, [P]),
         "dd_execute": (I, [P, I64, P, I, I64, P, I64, P, ctypes.c_uint]),
         "dd_execute_noalloc": (I, [P, I64, P, I, I64, P, I64, P]),
+        "dd_plan_set_tree": (I, [P, I]),
+        "dd_plan_get_tree_dm_limit": (I, [P, I, pp(D)]),
         "dd_server_set_timeout": (I, [P, D]),
         "dd_server_drain": (I, [P]),
         "dd_server_pause_next_launch": (I, [P, D]),
@@ -240,10 +243,24 @@ class Plan:
                "dd_plan_get_scrunch_factors")
         return out
 
-    def input_rows(self, nsamps_out, subband=False, scrunch=False):
+    def set_tree(self, chans_per_subband):
+        """The piecewise linear tree method (Sec. 3.1.1) with N' channels per
+        sub-band (a power of two, 2..128; 0 turns it off); execute with
+        tree=True."""
+        _check(_lib.dd_plan_set_tree(self._h, int(chans_per_subband)), "dd_plan_set_tree")
+
+    def tree_dm_limit(self, chans_per_subband):
+        """Eq. (tree_dm_limit): the piecewise diagonal DM for N' channels."""
+        v = ctypes.c_double()
+        _check(_lib.dd_plan_get_tree_dm_limit(self._h, int(chans_per_subband), ctypes.byref(v)),
+               "dd_plan_get_tree_dm_limit")
+        return v.value
+
+    def input_rows(self, nsamps_out, subband=False, scrunch=False, tree=False):
         """Input rows an execute of nsamps_out samples reads."""
         r = ctypes.c_int64()
-        flags = (DD_SUBBAND if subband else 0) | (DD_SCRUNCH if scrunch else 0)
+        flags = ((DD_SUBBAND if subband else 0) | (DD_SCRUNCH if scrunch else 0) |
+                 (DD_TREE if tree else 0))
         _check(_lib.dd_plan_get_input_rows(self._h, int(nsamps_out), flags, ctypes.byref(r)),
                "dd_plan_get_input_rows")
         return r.value
@@ -335,7 +352,8 @@ class Plan:
     def reset_kernel_timing(self):
         _check(_lib.dd_plan_reset_kernel_timing(self._h), "dd_plan_reset_kernel_timing")
 
-    def execute(self, inp, nbits, nsamps_out, out, stream=None, subband=False, scrunch=False):
+    def execute(self, inp, nbits, nsamps_out, out, stream=None, subband=False, scrunch=False,
+                tree=False):
         """Dedisperse ``nsamps_out`` samples of ``inp`` (rows = time, packed
         channel bytes or float channels) into ``out`` ([ndm][>= nsamps_out],
         uint32/int32 or float32).  Both on the device (torch CUDA tensors,
@@ -348,7 +366,7 @@ class Plan:
         if esize * 8 != getattr(self, "out_bits", 32):
             raise ValueError("output elements must be %d-bit" % getattr(self, "out_bits", 32))
         flags = ((DD_DEVICE_PTRS if idev else 0) | (DD_SUBBAND if subband else 0) |
-                 (DD_SCRUNCH if scrunch else 0))
+                 (DD_SCRUNCH if scrunch else 0) | (DD_TREE if tree else 0))
         _check(_lib.dd_execute(self._h, int(nsamps_out), ip, int(nbits), int(istride), op,
                                int(ostride // esize), _stream_ptr(stream), flags), "dd_execute")
         return out

@@ -808,6 +808,7 @@ dd_status exec_device(Plan& p, const ExecArgs& a) {
   if (fmt < 0) return DD_ERR_UNSUPPORTED_NBITS;
   dd_status s = ensure_device_tables(p);
   if (s != DD_OK) return s;
+  if (a.tree) return exec_tree(p, a);
   return a.subband ? exec_subband(p, a, fmt) : exec_direct(p, a, fmt);
 }
 
@@ -828,10 +829,13 @@ extern "C" dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void* in
   if (in_row_stride < row_bytes) return DD_ERR_INVALID_ARG;
   const bool sub = (flags & DD_SUBBAND) != 0;
   const bool scr = (flags & DD_SCRUNCH) != 0;
+  const bool tree = (flags & DD_TREE) != 0;
   if (sub && p->sb_chans <= 0) return DD_ERR_INVALID_ARG;
   if (scr && (sub || p->scrunch_max <= 0 || !(flags & DD_DEVICE_PTRS)))
     return DD_ERR_INVALID_ARG;
   if (scr && in_nbits > 4) return DD_ERR_UNSUPPORTED_NBITS;
+  if (tree && (sub || scr || p->tree_chans <= 0 || p->out_bits != 32)) return DD_ERR_INVALID_ARG;
+  if (tree && in_nbits == 32) return DD_ERR_UNSUPPORTED_NBITS;
   std::lock_guard<std::mutex> lk(p->mu);
   if (sub) {
     dd_status s = prepare_subband(*p);
@@ -841,8 +845,13 @@ extern "C" dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void* in
     dd_status s = prepare_scrunch(*p);
     if (s != DD_OK) return s;
   }
-  const int64_t rows = scr ? scrunch_input_rows(*p, nsamps_out)
-                           : nsamps_out + (sub ? p->sb_max_delay : p->max_delay);
+  if (tree) {
+    dd_status s = prepare_tree(*p);
+    if (s != DD_OK) return s;
+  }
+  const int64_t rows = scr    ? scrunch_input_rows(*p, nsamps_out)
+                       : tree ? nsamps_out + tree_input_extra(*p)
+                              : nsamps_out + (sub ? p->sb_max_delay : p->max_delay);
   ExecArgs a;
   a.nsamps_out = nsamps_out;
   a.in_nbits = in_nbits;
@@ -851,6 +860,7 @@ extern "C" dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void* in
   a.out_stride = out_stride;
   a.st = static_cast<cudaStream_t>(cuda_stream);
   a.subband = sub;
+  a.tree = tree;
   const size_t in_bytes = (size_t)(rows - 1) * in_row_stride + row_bytes;
   const int esz = p->out_bits / 8;
   if (esz != 4 && (in_nbits == 32 || scr)) return DD_ERR_INVALID_ARG;
@@ -868,7 +878,7 @@ extern "C" dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void* in
   if ((e = p->d_out.ensure(out_bytes)) != cudaSuccess) return cuda_status(e);
   a.in = p->d_in.p;
   a.out = p->d_out.p;
-  if (!sub) return exec_direct_host_out(*p, a, fmt, in, in_bytes, out);
+  if (!sub && !tree) return exec_direct_host_out(*p, a, fmt, in, in_bytes, out);
   if ((e = cudaMemcpyAsync(p->d_in.p, in, in_bytes, cudaMemcpyHostToDevice, a.st)) != cudaSuccess)
     return cuda_status(e);
   dd_status s = exec_device(*p, a);
@@ -937,6 +947,11 @@ extern "C" dd_status dd_plan_get_input_rows(dd_plan plan, int64_t nsamps_out, un
     dd_status s = prepare_subband(*p);
     if (s != DD_OK) return s;
     *rows = nsamps_out + p->sb_max_delay;
+  } else if (flags & DD_TREE) {
+    if (p->tree_chans <= 0) return DD_ERR_INVALID_ARG;
+    dd_status s = prepare_tree(*p);
+    if (s != DD_OK) return s;
+    *rows = nsamps_out + tree_input_extra(*p);
   } else {
     *rows = nsamps_out + p->max_delay;
   }

@@ -255,6 +255,13 @@ struct Plan {
   std::vector<ScrLevel> scr_levels;
   std::vector<int32_t> scr_factor;  // per trial
   DevBuf d_scr;                     // scrunched input of the level being run
+  // piecewise linear tree (Sec. 3.1.1): N' channels per sub-band (0 = off)
+  int tree_chans = 0;
+  bool tree_dirty = true, tree_dev_dirty = true;
+  std::vector<int32_t> tree_tab;   // [trial][sub-band] {stage-1 row, shift}
+  std::vector<int32_t> tree_roff;  // first stage-1 row of each sub-band (+ end)
+  int32_t tree_shift_max = 0;      // max_{d,n} dt''_n(d)
+  DevBuf d_tree_tab, d_tree_roff, d_tree_S;
   // host-pointer execute: output copies overlap the next part's compute
   cudaStream_t copy_st = nullptr;  // host-output path: copies out
   cudaStream_t in_st = nullptr;    // host-output path: input rows in
@@ -298,6 +305,7 @@ struct ExecArgs {
   int64_t out_stride;
   cudaStream_t st;
   bool subband;
+  bool tree = false;  // piecewise linear tree (Sec. 3.1.1)
 };
 dd_status exec_device(Plan& p, const ExecArgs& a);
 // Time-scrunched direct transform (device pointers); input rows needed.
@@ -305,6 +313,14 @@ dd_status exec_scrunch(Plan& p, const ExecArgs& a);
 dd_status prepare_scrunch(Plan& p);
 int64_t scrunch_input_rows(const Plan& p, int64_t nsamps_out);
 dd_status build_delays(Plan& p);
+// Eq. 3: samples of delay per unit DM of channel c (any c >= 0 whose
+// frequency is positive, including the band edge c = nchans).
+double partial_delay(double f0, double df, double dt, int c);
+// Piecewise linear tree (Sec. 3.1.1): host tables, input rows beyond the
+// gulp, and the two-stage execution on device buffers.
+dd_status prepare_tree(Plan& p);
+int64_t tree_input_extra(const Plan& p);
+dd_status exec_tree(Plan& p, const ExecArgs& a);
 void plan_init_band(Plan& p, int nchans, double dt, double f0, double df);
 
 // Build the segments and launch parameters for a direct transform over an

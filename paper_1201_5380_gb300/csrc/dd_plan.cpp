@@ -84,7 +84,7 @@ KernelTimer::~KernelTimer() {
 // channel 0).  The evaluation order (f, then 1/f^2 - 1/f0^2, then the
 // k_DM/dtau factor, then the DM product in the caller) is fixed, and the
 // library is compiled without FMA contraction, so the table is reproducible.
-static double partial_delay(double f0, double df, double dt, int c) {
+double partial_delay(double f0, double df, double dt, int c) {
   const double f = f0 + (double)c * df;
   return (kDispersionConst / dt) * (1.0 / (f * f) - 1.0 / (f0 * f0));
 }
@@ -115,6 +115,7 @@ dd_status build_delays(Plan& p) {
   p.sb_dirty = true;
   drop_stage_tabs(p, 7);
   p.scr_dirty = true;
+  p.tree_dirty = true;
   return DD_OK;
 }
 

@@ -18,7 +18,7 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def run_direct(plan, inp, nbits, nsamps, out_stride=None, subband=False, stream=None):
+def run_direct(plan, inp, nbits, nsamps, out_stride=None, subband=False, stream=None, tree=False):
     """Execute on the device; returns uint32 (or float32) [ndm][nsamps]."""
     torch = torch_cuda()
     d_in = to_dev(inp)
@@ -26,7 +26,7 @@ def run_direct(plan, inp, nbits, nsamps, out_stride=None, subband=False, stream=
     cols = out_stride or nsamps
     dtype = torch.float32 if nbits == 32 else torch.int32
     out = torch.full((ndm, cols), -7, dtype=dtype, device="cuda")
-    plan.execute(d_in, nbits, nsamps, out, stream=stream, subband=subband)
+    plan.execute(d_in, nbits, nsamps, out, stream=stream, subband=subband, tree=tree)
     torch.cuda.synchronize()
     assert plan.device_status() == 0
     o = out.cpu().numpy()
