@@ -279,14 +279,15 @@ __device__ __forceinline__ int64_t window_word(int64_t t0, int32_t s0, int lo_sl
   return (b / (4 * SPW)) * 4;
 }
 
-// Shared-memory layout (32-bit words), two buffers of each region:
+// Shared-memory layout (32-bit words):
 //   [0,4)            two mbarriers
-//   landing[1 or 2][cc][nww+4]     TMA destination: raw image windows (one
-//                                  buffer when the shifted copies are built
-//                                  from it, two when lanes read it directly)
-//   copies [2][cc*SPW][nww]        SPW lane-shifted copies of each window
+//   two buffers, each
+//     landing[cc][nww+4]           TMA destination: raw image windows, read
+//                                  by the sums as the unshifted copy
+//     copies [cc*(SPW-1)][nww]     the other SPW-1 lane-shifted copies of
+//                                  each window
 //   addr   [2][B*cc]               byte offset of each (trial, channel)
-//                                  window inside copies (lane 0, word 0)
+//                                  window inside its buffer (lane 0, word 0)
 //
 // The staging tables are built on the host per plan and geometry (they do
 // not depend on the time tile): per trial block its chunk size cc and window
@@ -326,8 +327,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
   // Chunk geometry and the staging layout it implies: the launch's, set up
   // once here, or (PBG) each trial block's, set up per work item.
   struct Geo {
-    int cc, cc_log, nww, nwl, landing_words, copy_words, n_entries, tpc_log, bc;
-    uint32_t* copies;
+    int cc, cc_log, nww, nwl, buf_words, n_entries, tpc_log, bc;
     uint32_t* s_addr;
   };
   auto make_geo = [&](int cc, int nww) {
@@ -336,14 +336,10 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
     g.cc_log = 31 - __clz(cc);
     g.nww = nww;  // window words (multiple of 4)
     g.nwl = nww + 4;
-    // with shifted copies the landing area is read only by the build, which
-    // the chunk's barrier ends before the next chunk's windows are requested:
-    // one landing buffer serves both (stride 0); without copies the sums read
-    // it, so it is double-buffered
-    g.copies = landing + (COPIES ? 1 : 2) * cc * g.nwl;
-    g.landing_words = COPIES ? 0 : cc * g.nwl;
-    g.copy_words = COPIES ? cc * SPW * nww : 0;
-    g.s_addr = g.copies + 2 * g.copy_words;
+    // one buffer: the landing windows (the sums read them as the unshifted
+    // copy), then the SPW-1 shifted copies built from them
+    g.buf_words = cc * g.nwl + (COPIES ? cc * (SPW - 1) * nww : 0);
+    g.s_addr = landing + 2 * g.buf_words;
     g.n_entries = B << g.cc_log;  // offsets per chunk
     // the builder threads of a channel: NT / cc of them
     g.tpc_log = (31 - __clz(NT)) - g.cc_log;
@@ -414,9 +410,8 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
     }
     const Geo G = PBG ? make_geo(bgeo.x, bgeo.y) : geo_launch;
     const int cc = G.cc, cc_log = G.cc_log, nww = G.nww, nwl = G.nwl;
-    uint32_t* const copies = G.copies;
     uint32_t* const s_addr = G.s_addr;
-    const int landing_words = G.landing_words, copy_words = G.copy_words;
+    const int buf_words = G.buf_words;
     const int n_entries = G.n_entries, tpc_log = G.tpc_log, bc = G.bc;
     const int nchunks = (nchan + cc - 1) >> cc_log;
     const uint32_t* __restrict__ atab =
@@ -457,7 +452,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       __syncwarp();
       if (words) {
         fence_proxy_async_smem();
-        tma_load_1d(smem_addr(landing + nb * landing_words + lane * nwl),
+        tma_load_1d(smem_addr(landing + nb * buf_words + lane * nwl),
                     img + (int64_t)cabs * row_words + wi, words * 4u, bar);
       }
     };
@@ -491,13 +486,15 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       }
       if (!COPIES) {
         if (c0 + cc > nchan) {
-          uint32_t* const land = landing + buf * landing_words;
+          uint32_t* const land = landing + buf * buf_words;
           for (int e = tid; e < (c0 + cc - nchan) * nwl; e += NT)
             land[(nchan - c0) * nwl + e] = 0u;
+          // a later bulk copy (async proxy) may land on these words
+          fence_proxy_async_smem();
         }
       } else {
-        const uint32_t* const land = landing + buf * landing_words;
-        uint32_t* const cp = copies + buf * copy_words;
+        uint32_t* const land = landing + buf * buf_words;
+        uint32_t* const cp = land + cc * nwl;
         const int c = bc;
         const int nq = (min(span, nww) + 3) >> 2;
         const bool live = c0 + c < nchan;
@@ -507,22 +504,23 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
           if (live) {
             w = *reinterpret_cast<const uint4*>(land + c * nwl + 4 * q);
             w4 = land[c * nwl + 4 * q + 4];
+          } else {
+            // a channel past the band: its (never copied) window reads zero
+            *reinterpret_cast<uint4*>(land + c * nwl + 4 * q) = w;
           }
-          uint32_t* dst = cp + c * SPW * nww + 4 * q;
+          uint32_t* dst = cp + c * (SPW - 1) * nww + 4 * q;
 #pragma unroll
-          for (int kap = 0; kap < SPW; ++kap) {
+          for (int kap = 1; kap < SPW; ++kap) {
             uint4 v;
-            if (kap == 0) {
-              v = w;
-            } else {
-              v.x = __funnelshift_r(w.x, w.y, kap * LW);
-              v.y = __funnelshift_r(w.y, w.z, kap * LW);
-              v.z = __funnelshift_r(w.z, w.w, kap * LW);
-              v.w = __funnelshift_r(w.w, w4, kap * LW);
-            }
-            *reinterpret_cast<uint4*>(dst + kap * nww) = v;
+            v.x = __funnelshift_r(w.x, w.y, kap * LW);
+            v.y = __funnelshift_r(w.y, w.z, kap * LW);
+            v.z = __funnelshift_r(w.z, w.w, kap * LW);
+            v.w = __funnelshift_r(w.w, w4, kap * LW);
+            *reinterpret_cast<uint4*>(dst + (kap - 1) * nww) = v;
           }
         }
+        // a later bulk copy (async proxy) may land on the zeroed words
+        if (!live) fence_proxy_async_smem();
       }
       __syncthreads();
       // (b) next chunk's TMA (its buffers were released by the barrier above)
@@ -530,9 +528,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       span = span_next;
       // (c) shift-and-sum over the chunk, four channels per group
       const uint32_t* const sa = s_addr + buf * n_entries;
-      const uint32_t lane_off =
-          (COPIES ? smem_addr(copies + buf * copy_words) : smem_addr(landing + buf * landing_words)) +
-          (uint32_t)lane * 4u;
+      const uint32_t lane_off = smem_addr(landing + buf * buf_words) + (uint32_t)lane * 4u;
       bool paired = false;
       if constexpr (FMT == FMT_NIB)
         paired = p.f0 == 1 && p.f1 >= 2 && (cc & 7) == 0 && (cc >> 3) <= (p.f1 >> 1);

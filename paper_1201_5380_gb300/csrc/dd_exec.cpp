@@ -243,7 +243,8 @@ static dd_status build_stage_tab(const TabSrc& src, int fmt, int cfg, int cc_cap
         const int cl = c % cc;
         uint32_t* a = at + (int64_t)(c / cc) * B * cc + cl;
         if (c >= src.nchan) {
-          const uint32_t zero = (uint32_t)(copies ? cl * spw * nww : cl * (nww + 4)) * 4u;
+          // the zeroed landing window of an absent channel
+          const uint32_t zero = (uint32_t)(cl * (nww + 4)) * 4u;
           for (int i = 0; i < B; ++i) a[(int64_t)i * cc] = zero;
           continue;
         }
@@ -254,8 +255,11 @@ static dd_status build_stage_tab(const TabSrc& src, int fmt, int cfg, int cc_cap
           const int64_t o = (int64_t)kPad + dl[(int64_t)d * src.dstride + c] - woff * spw;
           const int64_t om = o / spw;
           const int64_t kap = o & (spw - 1);
-          a[(int64_t)i * cc] = (uint32_t)(copies ? ((cl * spw + kap) * nww + om) * 4
-                                                 : (cl * (nww + 4) + om) * 4);
+          // the unshifted copy is the landing window; copy kap >= 1 follows
+          // the chunk's cc landing windows
+          a[(int64_t)i * cc] =
+              (uint32_t)(kap == 0 ? (cl * (nww + 4) + om) * 4
+                                  : ((int64_t)cc * (nww + 4) + (cl * (spw - 1) + kap - 1) * nww + om) * 4);
         }
         cr[2 * c] = (int32_t)woff;
         cr[2 * c + 1] = (int32_t)span;
@@ -430,14 +434,14 @@ static dd_status finish_launch(Plan& p, int fmt, int outk, int vmax, std::vector
   return DD_OK;
 }
 
-dd_status run_launch(Plan& p, LaunchPlan& L, cudaStream_t st) {
+dd_status run_launch(Plan& p, LaunchPlan& L, cudaStream_t st, int timer_kind) {
   if (L.lp.n_items == 0) return DD_OK;
   L.lp.status = static_cast<uint32_t*>(p.d_status.p);
   L.lp.next_item = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(p.d_status.p) + 8 +
                                                          8 * (p.launch_seq++ % kItemCounters));
   cudaError_t e0 = cudaMemsetAsync(L.lp.next_item, 0, 8, st);
   if (e0 != cudaSuccess) return cuda_status(e0);
-  KernelTimer kt(&p, 1, st);
+  KernelTimer kt(&p, timer_kind, st);
   return cuda_status(launch_dedisp(L.fmt, L.outk, L.wide, L.cfg, L.lp, L.grid, L.smem, st));
 }
 
@@ -800,7 +804,7 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
   LaunchPlan L2;
   s = finish_launch(p, fmt2, OUT_U32, (int)std::min<int64_t>(vmax1, INT_MAX), specs, vec, &L2);
   if (s != DD_OK) return s;
-  return run_launch(p, L2, a.st);
+  return run_launch(p, L2, a.st, DD_KERNEL_STAGE2);
 }
 
 dd_status exec_device(Plan& p, const ExecArgs& a) {

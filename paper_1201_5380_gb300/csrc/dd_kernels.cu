@@ -38,15 +38,14 @@ cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, bool
   return dispatch(fmt, outk, wide, cfg, pbg, nullptr, 0, smem, nullptr, nblk);
 }
 
-// Two mbarriers, the landing windows (cc x (nww+4); one buffer when shifted
-// copies are built from them, else two), then two buffers each of the SPW
-// shifted copies (cc x SPW x nww) and the address table (B x cc).
+// Two mbarriers, then two buffers each of the landing windows (cc x
+// (nww+4), the unshifted copy) and the other SPW-1 shifted copies (cc x
+// (SPW-1) x nww), then two address tables (B x cc).
 size_t dedisp_smem_bytes(int fmt, int cfg, int cc, int nww) {
   const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
-  const bool copied = fmt_spw(fmt) > 1;
-  const size_t copies = copied ? (size_t)cc * fmt_spw(fmt) * nww : 0;
-  const size_t landing = (copied ? 1u : 2u) * (size_t)cc * (nww + 4);
-  return 16u + 4u * (landing + 2u * (copies + (size_t)B * cc));
+  const size_t copies = (size_t)cc * (fmt_spw(fmt) - 1) * nww;
+  const size_t landing = (size_t)cc * (nww + 4);
+  return 16u + 4u * 2u * (landing + copies + (size_t)B * cc);
 }
 
 // ---------------------------------------------------------------------------
