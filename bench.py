@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -55,7 +56,11 @@ def _args():
                          "fixed tiling instead of the autotuner's (for profiler captures)")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the format sweep (1/4/8-bit and float input)")
-    ap.add_argument("--nbits", type=int, default=2, choices=[1, 2, 4, 8],
+    ap.add_argument("--profile-step", default="", choices=["", "subband", "tree"],
+                    help="run only warm-up + steps of the sub-band (N' = N'_DM = 32) or tree "
+                         "(N' = 32) method on the survey band and print their times: a short "
+                         "command for profiler captures of those kernels, not a bench line")
+    ap.add_argument("--nbits", type=int, default=2, choices=[1, 2, 4, 8, 32],
                     help="input bits per sample (the survey workload is 2-bit)")
     ap.add_argument("--dm-hi", type=float, default=1000.0,
                     help="largest trial DM (the survey workload: 1000)")
@@ -68,6 +73,8 @@ def _args():
 def _make_input(plan_dms, delays, G, max_delay, nbits=2):
     c = configs.SURVEY
     rows = G + max_delay
+    if nbits == 32:
+        return synth.normal_f32(c["seed"], 0, rows, c["nchans"])
     x = synth.uniform_packed(c["seed"], 0, rows, c["nchans"], nbits)
     for p in c["pulses"]:
         k = int(np.argmin(np.abs(plan_dms - p["dm"])))
@@ -145,6 +152,30 @@ DEDISP_TRAFFIC_2E17 = {
 }
 
 
+def host_cpu():
+    """The host's logical CPU count and model name (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu model")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or None,
+            "machine": platform.machine()}
+
+
 def cpu_oracle_rate(x, delays, G, seconds, nbits=2):
     """Time the CPU oracle (as it stands) on a bounded sample of the workload:
     trials evenly spaced over the list, all channels, a prefix of the gulp.
@@ -215,7 +246,7 @@ def run_reference(a, rank, world):
                    "survey band, %d-bit input, trial DMs 0-%g" % (nb, a.dm_hi),
                    "nchans": nchans, "ndm": int(delays.shape[0]), "gulp": G, "nbits": nb},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
-                         "kind": "oracle", "sample": desc},
+                         "kind": "oracle", "sample": desc, "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -397,7 +428,7 @@ def _boxcar_snr(row, t0):
     return best
 
 
-def run_subband(a, x, plan_direct, d_out_direct, G):
+def run_subband(a, x, plan_direct, d_out_direct, G, peak_adds):
     """Sub-band dedispersion (Sec. 4) on the survey band with N'_nu = N'_DM
     = 32, nominal DMs at each group's lowest trial (early edge) and at its
     middle trial (centred): throughput in direct-equivalent units and the
@@ -439,10 +470,13 @@ def run_subband(a, x, plan_direct, d_out_direct, G):
         if plan.device_status() != 0:
             raise RuntimeError("device-side bound flag set in the sub-band run")
         ms = ev[0].elapsed_time(ev[1]) / reps
-        k_ms, _ = plan.kernel_timing(1)
+        k1_ms, _ = plan.kernel_timing(1)
+        k2_ms, _ = plan.kernel_timing(2)
+        k_ms = k1_ms + k2_ms
         units = float(c["nchans"]) * plan.dm_count * G
-        adds = G * (c["nchans"] * -(-plan.dm_count // n_dm) +
-                    plan.dm_count * (c["nchans"] // n_sub))
+        adds1 = G * c["nchans"] * -(-plan.dm_count // n_dm)
+        adds2 = G * plan.dm_count * (c["nchans"] // n_sub)
+        adds = adds1 + adds2
         dms = plan.dms
         snr = []
         for p in c["pulses"]:
@@ -464,12 +498,93 @@ def run_subband(a, x, plan_direct, d_out_direct, G):
         key = "centred" if centred else "early_edge"
         res[key] = {"ms_per_step": ms, "kernels_ms": k_ms / reps,
                     "value": units / (ms / 1e3) / 1e9, "adds_per_step": adds,
-                    "adds_vs_direct": adds / units, "snr_loss": snr}
+                    "adds_vs_direct": adds / units, "snr_loss": snr,
+                    "stages": {
+                        "stage1": {"ms": k1_ms / reps, "adds": adds1, "lanes": "4-bit",
+                                   "frac_of_int_add_probe": adds1 / (k1_ms / reps / 1e3)
+                                   / peak_adds},
+                        "stage2": {"ms": k2_ms / reps, "adds": adds2, "lanes": "16-bit",
+                                   "frac_of_int_add_probe": adds2 / (k2_ms / reps / 1e3)
+                                   / peak_adds}}}
         del d_in, out
     res["unit"] = UNIT + " (direct-equivalent)"
     res["snr_note"] = ("best boxcar (1..256 samples) peak S/N at each injected pulse's trial; "
                        "app_b_ratio = mu^-1/2 (matched-filter loss for the smeared width) with "
                        "mu from the App. B bound over the largest DM error in the trial group")
+    return res
+
+
+def _time_execute(plan, run, reps=5):
+    """Mean CUDA-event time of `run` over reps calls after two warm-ups, and
+    the plan's own kernel times per call (first stage or direct, second
+    stage)."""
+    import torch
+    for _ in range(2):
+        run()
+    torch.cuda.synchronize()
+    plan.reset_kernel_timing()
+    plan.set_kernel_timing(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(reps):
+        run()
+    ev[1].record()
+    torch.cuda.synchronize()
+    plan.set_kernel_timing(False)
+    if plan.device_status() != 0:
+        raise RuntimeError("device-side bound flag set")
+    k1, _ = plan.kernel_timing(1)
+    k2, _ = plan.kernel_timing(2)
+    return ev[0].elapsed_time(ev[1]) / reps, k1 / reps, k2 / reps
+
+
+def run_tree(a, x, G, peak_adds):
+    """The piecewise linear tree (Sec. 3.1.1) on the survey gulp over its DM
+    range: every trial of the rule's list below the piecewise diagonal DM of
+    Eq. (tree_dm_limit), for N' = 32 and 64, against the direct transform of
+    the same trials on the same input.  Adds per step: the tree's
+    nchans * log2(N') per sample (stage 1, over the stage-1 rows) plus
+    ndm * nchans / N' (stage 2)."""
+    import torch
+    import paper_1201_5380_gb300 as dd
+
+    c = configs.SURVEY
+    res = {"workload": "survey band (1024 ch, 2-bit, 2^19 samples), trials of the rule's list "
+                       "below the piecewise diagonal DM", "unit": UNIT + " (direct-equivalent)"}
+    full = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
+    for nsub in (32, 64):
+        lim = full.tree_dm_limit(nsub)
+        dms = full.dms[full.dms < lim]
+        tree = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dms=dms)
+        tree.set_tree(nsub)
+        direct = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dms=dms)
+        rows = max(tree.input_rows(G, tree=True), direct.max_delay + G)
+        d_in = torch.from_numpy(np.ascontiguousarray(x[:rows])).cuda()
+        o_t = torch.empty((len(dms), G), dtype=torch.int32, device="cuda")
+        o_d = torch.empty((len(dms), G), dtype=torch.int32, device="cuda")
+        t_ms, t1_ms, t2_ms = _time_execute(tree, lambda: tree.execute(d_in, 2, G, o_t, tree=True))
+        d_ms, dk_ms, _ = _time_execute(direct, lambda: direct.execute(d_in, 2, G, o_d))
+        units = float(c["nchans"]) * len(dms) * G
+        len1 = tree.input_rows(G, tree=True) - (nsub - 1)
+        adds1 = c["nchans"] * int(np.log2(nsub)) * len1
+        adds2 = len(dms) * (c["nchans"] // nsub) * G
+        adds = adds1 + adds2
+        res["nsub_%d" % nsub] = {
+            "dm_limit": lim, "ndm": len(dms), "dm_max": float(dms[-1]),
+            "ms_per_step": t_ms, "kernels_ms": t1_ms + t2_ms,
+            "value": units / (t_ms / 1e3) / 1e9,
+            "direct_ms_per_step": d_ms, "direct_kernel_ms": dk_ms,
+            "speedup_vs_direct_step": d_ms / t_ms,
+            "adds_per_step": adds, "adds_vs_direct": adds / units,
+            "stages": {"stage1": {"ms": t1_ms, "adds": adds1, "lanes": "16-bit pairs",
+                                  "frac_of_int_add_probe": adds1 / (t1_ms / 1e3) / peak_adds},
+                       "stage2": {"ms": t2_ms, "adds": adds2, "lanes": "32-bit",
+                                  "frac_of_int_add_probe": adds2 / (t2_ms / 1e3) / peak_adds}},
+            "app_a_smear_us_at_dm_max": 1e6 * 0.75 * float(dms[-1]) * 4.148808e3 / c["f0"] ** 2
+            * (nsub / c["nchans"]) ** 2 * (c["df"] * c["nchans"] / c["f0"]) ** 2
+            / (1 + c["df"] * c["nchans"] / c["f0"]) ** 4,
+        }
+        del d_in, o_t, o_d
     return res
 
 
@@ -675,6 +790,44 @@ def replica_throughput(local_ms, units_per_rank, world, device):
     return t_ms, world * units_per_rank / (t_ms / 1e3) / 1e9
 
 
+def profile_step(a, plan, x, G, dev):
+    """Warm-up + steps of one method's execute on the survey band, for
+    profiler captures of its kernels (sub-band: N' = N'_DM = 32; tree: N' =
+    32 over the trials below the piecewise diagonal DM)."""
+    import torch
+    import paper_1201_5380_gb300 as dd
+
+    c = configs.SURVEY
+    if a.profile_step == "subband":
+        p = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=a.dm_hi),
+                    subband=(32, 32))
+        rows, kw = G + p.subband_max_delay, dict(subband=True)
+    else:
+        dms = plan.dms[plan.dms < plan.tree_dm_limit(32)]
+        p = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dms=dms)
+        p.set_tree(32)
+        rows, kw = p.input_rows(G, tree=True), dict(tree=True)
+    xx = np.ascontiguousarray(x[:rows]) if x.shape[0] >= rows else np.concatenate(
+        [x, np.zeros((rows - x.shape[0],) + x.shape[1:], x.dtype)])
+    d_in = torch.from_numpy(xx).to(dev)
+    out = torch.empty((p.dm_count, G), dtype=torch.int32, device=dev)
+    for _ in range(a.warmup):
+        p.execute(d_in, a.nbits, G, out, **kw)
+    torch.cuda.synchronize(dev)
+    p.reset_kernel_timing()
+    p.set_kernel_timing(True)
+    for _ in range(a.steps):
+        p.execute(d_in, a.nbits, G, out, **kw)
+    torch.cuda.synchronize(dev)
+    p.set_kernel_timing(False)
+    k1, n1 = p.kernel_timing(1)
+    k2, n2 = p.kernel_timing(2)
+    print(json.dumps({"profile_step": a.profile_step, "gulp": G, "ndm": p.dm_count,
+                      "stage1_ms": k1 / max(n1, 1), "stage2_ms": k2 / max(n2, 1),
+                      "status": p.device_status()}))
+    return 0
+
+
 def run_ours(a, rank, world, local_rank):
     import torch
     import paper_1201_5380_gb300 as dd
@@ -698,8 +851,11 @@ def run_ours(a, rank, world, local_rank):
     in_bytes = x.nbytes
     out_bytes = ndm * G * 4
     d_in = torch.from_numpy(x).to(dev)
-    out = torch.empty((ndm, G), dtype=torch.int32, device=dev)
+    out_dt = torch.float32 if nb == 32 else torch.int32
+    out = torch.empty((ndm, G), dtype=out_dt, device=dev)
     stream = torch.cuda.current_stream(dev)
+    if a.profile_step:
+        return profile_step(a, plan, x, G, dev)
 
     for _ in range(a.warmup):
         plan.execute(d_in, nb, G, out, stream=stream)
@@ -738,9 +894,10 @@ def run_ours(a, rank, world, local_rank):
     ms_step = total_ms / a.steps
 
     # end to end through the C ABI with host buffers (pinned), copies timed
-    h_in = torch.empty(x.shape, dtype=torch.uint8, pin_memory=True)
+    h_in = torch.empty(x.shape, dtype=torch.float32 if nb == 32 else torch.uint8,
+                       pin_memory=True)
     h_in.numpy()[:] = x
-    h_out = torch.empty((ndm, G), dtype=torch.int32, pin_memory=True)
+    h_out = torch.empty((ndm, G), dtype=out_dt, pin_memory=True)
     hin, hout = h_in.numpy(), h_out.numpy()
     plan.execute(hin, nb, G, hout)
     barrier()
@@ -751,7 +908,7 @@ def run_ours(a, rank, world, local_rank):
     e2e_ms, e2e_value = replica_throughput(e2e_s * 1e3, units, world, dev)
     e2e_s = e2e_ms / 1e3
     if not np.array_equal(hout.view(np.uint32)[:, :64],
-                          out[:, :64].cpu().numpy().view(np.uint32)):
+                          out[:, :64].cpu().numpy().view(np.uint32), equal_nan=False):
         raise RuntimeError("host-path output differs from device-path output")
 
     # roofline of the dedispersion kernel: algorithmic adds per launch over its
@@ -800,9 +957,10 @@ def run_ours(a, rank, world, local_rank):
     if rank == 0 and world == 1 and not a.no_subband and default:
         line["scrunch"] = run_scrunch(a, x, G, ms_step)
         line["scaled_output"] = run_scaled(a, x, G)
-        line["subband"] = run_subband(a, x, plan, out, G)
+        line["subband"] = run_subband(a, x, plan, out, G, peak_adds)
         line["subband"]["speedup_vs_direct_kernels"] = (
             k_ms / line["subband"]["early_edge"]["kernels_ms"])
+        line["tree"] = run_tree(a, x, G, peak_adds)
     if rank == 0 and world == 1 and not a.no_sweep and default:
         line["format_sweep"] = run_format_sweep(a)
     if rank == 0 and world == 1 and not a.no_serving and default:
@@ -816,7 +974,7 @@ def run_ours(a, rank, world, local_rank):
         oracle_delays = oracle.delay_table(nchans, c["f0"], c["df"], c["dt"], plan.dms)
         v, cores, desc, secs = cpu_oracle_rate(x, oracle_delays, G, a.cpu_seconds, nb)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": desc, "seconds": secs}
+                                "sample": desc, "seconds": secs, "host": host_cpu()}
     if rank == 0:
         print(json.dumps(line))
     return 0

@@ -240,9 +240,12 @@ dd_status dd_plan_get_device_status(dd_plan plan, uint32_t *flags);
  * bracketed by CUDA events on its own stream.  get_kernel_timing synchronises
  * on those events and returns the device time (ms) and launch count of one
  * kernel kind since the last reset: kind 0 = corner turn (unpack/transpose
- * into the staged image), 1 = dedispersion kernel.  reset clears both. */
+ * into the staged image), 1 = dedispersion kernel (direct, or the first
+ * stage of the sub-band and tree methods), 2 = the second stage of the
+ * sub-band and tree methods.  reset clears all. */
 #define DD_KERNEL_CORNER_TURN 0
 #define DD_KERNEL_DEDISP 1
+#define DD_KERNEL_STAGE2 2
 dd_status dd_plan_set_kernel_timing(dd_plan plan, int enable);
 dd_status dd_plan_get_kernel_timing(dd_plan plan, int kind, double *total_ms,
                                     int64_t *launches);
@@ -416,10 +419,12 @@ dd_status dd_server_set_timeout(dd_server server, double timeout_ms);
 dd_status dd_server_drain(dd_server server);
 
 /* Queue a pause of ms milliseconds (at most 60 s) on the compute stream
- * before the transform of the next launch.  The pause is a host callback
- * in the stream, with no device work: it makes a launch late on purpose, so
- * that deadlines and the scheduler's handling of slow launches can be
- * exercised without disturbing the GPU. */
+ * behind the transform of the next launch, before its completion is
+ * signalled.  The pause is a host callback in the stream, with no device
+ * work: it makes a launch late on purpose, so that deadlines and the
+ * scheduler's handling of slow launches can be exercised without disturbing
+ * the GPU.  (A request with host_out in pageable memory makes the launch's
+ * own output copy wait on the host, pause included.) */
 dd_status dd_server_pause_next_launch(dd_server server, double ms);
 
 /* Register a beam: its plan (band, DM list; must outlive the server), input

@@ -241,8 +241,8 @@ struct Plan {
     cudaEvent_t a, b;
   };
   std::vector<TimedLaunch> timed;
-  double timed_ms[2] = {0.0, 0.0};
-  int64_t timed_n[2] = {0, 0};
+  double timed_ms[3] = {0.0, 0.0, 0.0};  // per kind (DD_KERNEL_*)
+  int64_t timed_n[3] = {0, 0, 0};
   // time-scrunching (Sec. 2.2): 0 = off, else the largest factor; trials at
   // one factor form a level, run by a child plan at resolution s*dt
   int out_bits = 32;  // bits per output sample of dd_execute (8, 16 or 32)
@@ -373,7 +373,8 @@ bool out_vec_ok(const void* out, int64_t stride_elems, int esz);
 dd_status plan_direct_launch(Plan& p, int fmt, int outk, int vmax,
                              const std::vector<DirectJob>& jobs, LaunchPlan* lpl,
                              std::vector<std::shared_ptr<StageTab>>* tabs = nullptr);
-dd_status run_launch(Plan& p, LaunchPlan& lpl, cudaStream_t st);
+// timer_kind: the DD_KERNEL_* kind the launch is timed under
+dd_status run_launch(Plan& p, LaunchPlan& lpl, cudaStream_t st, int timer_kind = 1);
 // The plan's staging tables of `src` (kind 0 direct, 1/2 sub-band stage)
 // for a launch geometry, built on first use and uploaded when asked; null
 // with *err set if a window would not fit the geometry.  Without upload

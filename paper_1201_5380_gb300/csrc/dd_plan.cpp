@@ -541,7 +541,7 @@ dd_status dd_plan_set_kernel_timing(dd_plan plan, int enable) {
 
 dd_status dd_plan_get_kernel_timing(dd_plan plan, int kind, double* total_ms, int64_t* launches) {
   Plan* p = reinterpret_cast<Plan*>(plan);
-  if (!p || kind < 0 || kind > 1) return DD_ERR_INVALID_ARG;
+  if (!p || kind < 0 || kind > 2) return DD_ERR_INVALID_ARG;
   drain_timing(*p);
   if (total_ms) *total_ms = p->timed_ms[kind];
   if (launches) *launches = p->timed_n[kind];
@@ -552,8 +552,10 @@ dd_status dd_plan_reset_kernel_timing(dd_plan plan) {
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (!p) return DD_ERR_INVALID_ARG;
   drain_timing(*p);
-  p->timed_ms[0] = p->timed_ms[1] = 0.0;
-  p->timed_n[0] = p->timed_n[1] = 0;
+  for (int k = 0; k < 3; ++k) {
+    p->timed_ms[k] = 0.0;
+    p->timed_n[k] = 0;
+  }
   return DD_OK;
 }
 

@@ -307,16 +307,6 @@ struct dd_server_s {
       fail(take, *err);
       return 0;
     }
-    if (pause_next_ms > 0.0) {
-      L->pause_ms = pause_next_ms;
-      pause_next_ms = 0.0;
-      e = cudaLaunchHostFunc(comp, pause_host, &L->pause_ms);
-      if (e != cudaSuccess) {
-        *err = cuda_status(e);
-        fail(take, *err);
-        return 0;
-      }
-    }
     // one batched launch over every admitted beam
     dd_batch_clear(batch);
     dd_status s = DD_OK;
@@ -340,7 +330,14 @@ struct dd_server_s {
       r.n_out = nouts[i];
       any_host = any_host || r.host_out != nullptr;
     }
-    e = cudaLaunchHostFunc(comp, stamp, &L->t_compute);
+    // a requested pause holds the launch back after its transform is queued
+    // (so that none of the launch's own set-up waits for it)
+    if (pause_next_ms > 0.0) {
+      L->pause_ms = pause_next_ms;
+      pause_next_ms = 0.0;
+      e = cudaLaunchHostFunc(comp, pause_host, &L->pause_ms);
+    }
+    if (e == cudaSuccess) e = cudaLaunchHostFunc(comp, stamp, &L->t_compute);
     cudaStream_t last = comp;
     if (e == cudaSuccess && any_host) {
       e = cudaEventCreateWithFlags(&ev_comp, cudaEventDisableTiming);

@@ -269,7 +269,6 @@ dd_status exec_tree(Plan& p, const ExecArgs& a) {
   const int64_t pitch = ((tiles * T + 63) / 64) * 64;    // samples
   const int rows = p.tree_roff[nsb];
   if ((e = p.d_tree_S.ensure((size_t)rows * pitch * 2)) != cudaSuccess) return cuda_status(e);
-  KernelTimer kt(&p, 1, a.st);
   TreeS1 s1;
   s1.in = static_cast<const uint8_t*>(a.in);
   s1.in_stride = a.in_row_stride;
@@ -280,7 +279,10 @@ dd_status exec_tree(Plan& p, const ExecArgs& a) {
   s1.roff = static_cast<const int32_t*>(p.d_tree_roff.p);
   s1.len1 = len1;
   s1.nbits = a.in_nbits;
-  if ((e = stage1(Np, s1, tiles, nsb, a.st)) != cudaSuccess) return cuda_status(e);
+  {
+    KernelTimer kt(&p, DD_KERNEL_DEDISP, a.st);
+    if ((e = stage1(Np, s1, tiles, nsb, a.st)) != cudaSuccess) return cuda_status(e);
+  }
   TreeS2 s2;
   s2.S = static_cast<const uint16_t*>(p.d_tree_S.p);
   s2.s_pitch = pitch;
@@ -293,6 +295,7 @@ dd_status exec_tree(Plan& p, const ExecArgs& a) {
   const int64_t t2 = (a.nsamps_out + 32 * kS2K - 1) / (32 * kS2K);
   const dim3 grid((unsigned)t2, (unsigned)((n + kS2Warps - 1) / kS2Warps));
   const size_t smem = (size_t)kS2Warps * nsb * sizeof(int2);
+  KernelTimer kt(&p, DD_KERNEL_STAGE2, a.st);
   k_tree_stage2<<<grid, kS2Warps * 32, smem, a.st>>>(s2);
   return cuda_status(cudaGetLastError());
 }
