@@ -35,8 +35,11 @@ namespace {
 // Output samples per stage-1 block: the two shared buffers of N' rows x
 // (T + N') / 2 words stay near 35 KB each, so several blocks share an SM.
 __host__ __device__ constexpr int tree_tile(int nsub) { return nsub <= 32 ? 512 : (nsub == 64 ? 256 : 128); }
-__host__ __device__ constexpr int tree_words(int nsub) { return ((tree_tile(nsub) + nsub) / 2) | 1; }  // odd pitch
-constexpr int kTreeThreads = 256;
+__host__ __device__ constexpr int tree_words(int nsub) { return ((tree_tile(nsub) + nsub) / 2) | 1; }
+// Row pitch: the WW loaded words, then zero words that the shifted reads of
+// the last words run into (a pass reads at most 3 N'/8 + 3 words ahead), odd.
+__host__ __device__ constexpr int tree_pitch(int nsub) { return (tree_words(nsub) + nsub / 2 + 4) | 1; }
+constexpr int kTreeThreads = 512;
 constexpr int kMaxTreeChans = 128;
 
 struct TreeS1 {
@@ -47,87 +50,187 @@ struct TreeS1 {
   uint32_t* S;            // stage-1 rows, two 16-bit samples per word
   int64_t s_pitch;        // words per S row
   const int32_t* roff;    // first S row of each sub-band (+ end)
-  int64_t len1;           // samples per S row that stage 2 reads
   int nbits;
+  int nsb;                // sub-bands
 };
 
 // Eq. (shuffle) and Eq. (tree_integer_delay), truncated divisions.
 __device__ __forceinline__ int tree_phi(int r, int v) { return (v & 1) * r + v / 2 + (v / (2 * r)) * r; }
 __device__ __forceinline__ int tree_theta(int r, int v) { return ((v & (2 * r - 1)) + 1) >> 1; }
 
+// Where the last pass writes: stage-1 rows r0 .. r0 + nrow - 1 (the trails
+// 0 .. nrow - 1 of the sub-band), words of this tile from S.
+struct TreeOut {
+  uint32_t* S;
+  int64_t s_pitch;
+  int r0, nrow;
+};
+
+// Words of a row shifted by an odd sample: the high half of w0 and the low
+// half of w1 (two 16-bit samples per word, earlier sample low).
+__device__ __forceinline__ uint32_t half_shift(uint32_t w0, uint32_t w1) {
+  return __funnelshift_r(w0, w1, 16);
+}
+
+// Two steps of the tree at once, steps i and i + 1 (radix R = 2^i): in each
+// block of 4R rows, output K = 4m + sub takes trail m of its four quarters
+// j = 0..3, quarter j shifted by j*m plus 0, sub/2, (sub+1)/2, sub samples
+// (j = 0, 1, 2, 3): the composition of the two steps' Theta and Phi.
+template <int NSUB, int R, bool LAST>
+__device__ __forceinline__ void tree_radix4(const uint32_t* src, uint32_t* dst, const TreeOut& o) {
+  constexpr int T = tree_tile(NSUB), WW = tree_words(NSUB), PW = tree_pitch(NSUB);
+  constexpr int QN = LAST ? T / 2 : WW;  // the last pass writes only the tile
+  for (int e = threadIdx.x; e < (NSUB / 4) * QN; e += kTreeThreads) {
+    const int g = e / QN;
+    const int q = e - g * QN;
+    const int sb = g / R, m = g % R;
+    const int o0 = 4 * g;
+    if (LAST && o0 >= o.nrow) continue;
+    const uint32_t* q0 = src + ((4 * sb + 0) * R + m) * PW + q;
+    const uint32_t* q1 = src + ((4 * sb + 1) * R + m) * PW + q + (m >> 1);
+    const uint32_t* q2 = src + ((4 * sb + 2) * R + m) * PW + q + m;
+    const uint32_t* q3 = src + ((4 * sb + 3) * R + m) * PW + q + ((3 * m) >> 1);
+    const int ps = (m & 1) * 16;  // quarters 1 and 3 start on an odd sample when m is odd
+    const uint32_t a = q0[0];
+    const uint32_t b0 = __funnelshift_r(q1[0], q1[1], ps), b1 = __funnelshift_r(q1[1], q1[2], ps);
+    const uint32_t c0 = q2[0], c1 = q2[1];
+    const uint32_t d0 = __funnelshift_r(q3[0], q3[1], ps), d1 = __funnelshift_r(q3[1], q3[2], ps);
+    const uint32_t d2 = __funnelshift_r(q3[2], q3[3], ps);
+    const uint32_t b_1 = half_shift(b0, b1), c_1 = half_shift(c0, c1);
+    uint32_t r[4];
+    r[0] = a + b0 + c0 + d0;
+    r[1] = a + b0 + c_1 + half_shift(d0, d1);
+    r[2] = a + b_1 + c_1 + d1;
+    r[3] = a + b_1 + c1 + half_shift(d1, d2);
+#pragma unroll
+    for (int sub = 0; sub < 4; ++sub) {
+      if (LAST) {
+        if (o0 + sub < o.nrow) o.S[(int64_t)(o.r0 + o0 + sub) * o.s_pitch + q] = r[sub];
+      } else {
+        dst[(o0 + sub) * PW + q] = r[sub];
+      }
+    }
+  }
+}
+
+// One step (radix R = 2^i): outputs 2v and 2v + 1 take row lo and row hi = lo
+// + R of their block of 2R rows, hi shifted by s = v mod R and s + 1
+// samples (Theta of Eq. tree_integer_delay; lo and hi are Phi of Eq. shuffle).
+template <int NSUB, int R, bool LAST>
+__device__ __forceinline__ void tree_radix2(const uint32_t* src, uint32_t* dst, const TreeOut& o) {
+  constexpr int T = tree_tile(NSUB), WW = tree_words(NSUB), PW = tree_pitch(NSUB);
+  constexpr int QN = LAST ? T / 2 : WW;
+  for (int e = threadIdx.x; e < (NSUB / 2) * QN; e += kTreeThreads) {
+    const int v = e / QN;
+    const int q = e - v * QN;
+    const int o0 = 2 * v;
+    if (LAST && o0 >= o.nrow) continue;
+    const int lo = tree_phi(R, 2 * v), hi = tree_phi(R, 2 * v + 1);
+    const int sft = tree_theta(R, 2 * v);  // output 2v + 1: sft + 1
+    const uint32_t a = src[lo * PW + q];
+    const uint32_t* h = src + hi * PW + q + (sft >> 1);
+    const int ps = (sft & 1) * 16;
+    const uint32_t h0 = __funnelshift_r(h[0], h[1], ps), h1 = __funnelshift_r(h[1], h[2], ps);
+    const uint32_t r0 = a + h0, r1 = a + half_shift(h0, h1);
+    if (LAST) {
+      o.S[(int64_t)(o.r0 + o0) * o.s_pitch + q] = r0;
+      if (o0 + 1 < o.nrow) o.S[(int64_t)(o.r0 + o0 + 1) * o.s_pitch + q] = r1;
+    } else {
+      dst[o0 * PW + q] = r0;
+      dst[(o0 + 1) * PW + q] = r1;
+    }
+  }
+}
+
+// Steps I .. log2 N' - 1, reading src and writing dst (buffers alternate).
+template <int NSUB, int I>
+__device__ __forceinline__ void tree_passes(uint32_t* src, uint32_t* dst, const TreeOut& o) {
+  constexpr int M = (NSUB >= 2) + (NSUB >= 4) + (NSUB >= 8) + (NSUB >= 16) + (NSUB >= 32) +
+                    (NSUB >= 64) + (NSUB >= 128);  // log2 N'
+  if constexpr (I + 1 < M) {
+    tree_radix4<NSUB, (1 << I), I + 2 == M>(src, dst, o);
+    if constexpr (I + 2 < M) {
+      __syncthreads();
+      tree_passes<NSUB, I + 2>(dst, src, o);
+    }
+  } else if constexpr (I < M) {
+    tree_radix2<NSUB, (1 << I), true>(src, dst, o);
+  }
+}
+
 template <int NSUB>
 __global__ void __launch_bounds__(kTreeThreads) k_tree_stage1(const TreeS1 p) {
   constexpr int T = tree_tile(NSUB);
   constexpr int WW = tree_words(NSUB);
+  constexpr int PW = tree_pitch(NSUB);
+  constexpr int NWARP = kTreeThreads / 32;
   extern __shared__ uint32_t sm[];
   uint32_t* buf0 = sm;
-  uint32_t* buf1 = sm + NSUB * WW;
-  const int n = blockIdx.y;
-  const int64_t t0 = (int64_t)blockIdx.x * T;
+  uint32_t* buf1 = sm + NSUB * PW;
+  // blocks in order (tile, sub-band), sub-band fastest: the blocks running
+  // together read whole input rows between them
+  const int n = (int)(blockIdx.x % p.nsb);
+  const int64_t t0 = (int64_t)(blockIdx.x / p.nsb) * T;
   const int tid = threadIdx.x;
-  const int c0 = n * NSUB;
-  const uint32_t vmask = (1u << p.nbits) - 1u;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int nb = p.nbits;
+  const uint32_t vmask = (1u << nb) - 1u;
 
-  // (a) unpack rows t0 .. t0 + 2 WW - 1 of the sub-band's channels into 16-bit
-  //     lanes (consecutive threads take consecutive channels of one row)
+  // (a) unpack: a thread takes two consecutive rows (time samples) of the
+  //     sub-band at a time and writes each channel's pair of samples as one
+  //     word of that channel's row (16-bit lanes, earlier sample low)
   {
-    uint16_t* a16 = reinterpret_cast<uint16_t*>(buf0);
-    for (int e = tid; e < NSUB * 2 * WW; e += kTreeThreads) {
-      const int c = e % NSUB;
-      const int tl = e / NSUB;
-      const int64_t t = t0 + tl;
-      uint32_t v = 0u;
-      if (t < p.in_rows) {
-        const int64_t bit = (int64_t)(c0 + c) * p.nbits;
-        const uint8_t byte = __ldg(p.in + t * p.in_stride + (bit >> 3));
-        v = ((uint32_t)byte >> (bit & 7)) & vmask;
-        if (!__ldg(p.mask + c0 + c)) v = 0u;
+    const int64_t bit0 = (int64_t)n * NSUB * nb;  // a multiple of 8 unless N'*nbits < 8
+    const int sub_bits = NSUB * nb;
+    const bool words = (sub_bits % 32) == 0 &&
+                       ((reinterpret_cast<uintptr_t>(p.in) | (uintptr_t)p.in_stride |
+                         (uintptr_t)(bit0 >> 3)) & 3) == 0;
+    for (int q = tid; q < WW; q += kTreeThreads) {
+      const int64_t t = t0 + 2 * q;
+      const uint8_t* r0 = p.in + t * p.in_stride + (bit0 >> 3);
+      const uint8_t* r1 = r0 + p.in_stride;
+      const bool ok0 = t < p.in_rows, ok1 = t + 1 < p.in_rows;
+      if (words) {
+        for (int w = 0; w < sub_bits / 32; ++w) {
+          const uint32_t x0 = ok0 ? __ldg(reinterpret_cast<const uint32_t*>(r0) + w) : 0u;
+          const uint32_t x1 = ok1 ? __ldg(reinterpret_cast<const uint32_t*>(r1) + w) : 0u;
+          for (int j = 0; j < 32 / nb; ++j) {
+            const int c = w * (32 / nb) + j;
+            buf0[c * PW + q] = ((x0 >> (j * nb)) & vmask) | (((x1 >> (j * nb)) & vmask) << 16);
+          }
+        }
+      } else {
+        const int sh = (int)(bit0 & 7);
+        for (int c = 0; c < NSUB; ++c) {
+          const int b = sh + c * nb;
+          const uint32_t x0 = ok0 ? ((uint32_t)__ldg(r0 + (b >> 3)) >> (b & 7)) & vmask : 0u;
+          const uint32_t x1 = ok1 ? ((uint32_t)__ldg(r1 + (b >> 3)) >> (b & 7)) & vmask : 0u;
+          buf0[c * PW + q] = x0 | (x1 << 16);
+        }
       }
-      a16[c * 2 * WW + tl] = (uint16_t)v;
     }
+    // the zero words past each row, in both buffers (never written again)
+    for (int e = tid; e < 2 * NSUB * (PW - WW); e += kTreeThreads) {
+      const int row = e / (PW - WW);
+      sm[row * PW + WW + (e - row * (PW - WW))] = 0u;
+    }
+    __syncthreads();
+    // the kill mask: a killed channel's row reads zero
+    for (int c = warp; c < NSUB; c += NWARP)
+      if (!__ldg(p.mask + n * NSUB + c))
+        for (int q = lane; q < WW; q += 32) buf0[c * PW + q] = 0u;
   }
   __syncthreads();
 
-  // (b) the log2 N' steps, out of place between the two buffers
-  uint32_t* src = buf0;
-  uint32_t* dst = buf1;
-#pragma unroll 1
-  for (int r = 1; r < NSUB; r *= 2) {
-    for (int e = tid; e < NSUB * WW; e += kTreeThreads) {
-      const int o = e / WW;
-      const int q = e - o * WW;
-      const int v = o >> 1;
-      const uint32_t* lo = src + tree_phi(r, 2 * v) * WW;
-      const uint32_t* hi = src + tree_phi(r, 2 * v + 1) * WW;
-      const int th = tree_theta(r, o);
-      const int qq = q + (th >> 1);
-      // words past the buffer hold samples beyond the loaded rows: every
-      // output they reach is past the tile's last sample (t0 + T - 1 needs
-      // input only up to t0 + T + N' - 2 < t0 + 2 WW)
-      const uint32_t b0 = qq < WW ? hi[qq] : 0u;
-      uint32_t b = b0;
-      if (th & 1) {
-        const uint32_t b1 = qq + 1 < WW ? hi[qq + 1] : 0u;
-        b = __funnelshift_r(b0, b1, 16);
-      }
-      dst[o * WW + q] = lo[q] + b;
-    }
-    __syncthreads();
-    uint32_t* sw = src;
-    src = dst;
-    dst = sw;
-  }
-
-  // (c) the trails stage 2 reads, T samples of each
-  const int r0 = __ldg(p.roff + n);
-  const int nrow = __ldg(p.roff + n + 1) - r0;
-  const int64_t w0 = t0 / 2;
-  const int64_t wend = (p.len1 + 1) / 2;
-  for (int e = tid; e < nrow * (T / 2); e += kTreeThreads) {
-    const int d = e / (T / 2);
-    const int q = e - d * (T / 2);
-    if (w0 + q < wend) p.S[(int64_t)(r0 + d) * p.s_pitch + w0 + q] = src[d * WW + q];
-  }
+  // (b) the log2 N' steps, two at a time where it can (a radix-4 pass), out
+  //     of place between the two buffers; the last pass writes the trails
+  //     stage 2 reads straight to global memory
+  TreeOut o;
+  o.r0 = __ldg(p.roff + n);
+  o.nrow = __ldg(p.roff + n + 1) - o.r0;
+  o.S = p.S + t0 / 2;
+  o.s_pitch = p.s_pitch;
+  tree_passes<NSUB, 0>(buf0, buf1, o);
 }
 
 struct TreeS2 {
@@ -147,8 +250,11 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_tree_stage2(const TreeS2 p) {
   extern __shared__ int2 s_tab[];
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int d0 = blockIdx.y * kS2Warps;
-  const int64_t t0 = (int64_t)blockIdx.x * (32 * kS2K);
+  // blocks in order (time tile, trial block), trial block fastest: the
+  // blocks running together read the same stage-1 tiles, from L2
+  const int ntb = (p.ndm + kS2Warps - 1) / kS2Warps;
+  const int d0 = (int)(blockIdx.x % ntb) * kS2Warps;
+  const int64_t t0 = (int64_t)(blockIdx.x / ntb) * (32 * kS2K);
   const int nd = min(kS2Warps, p.ndm - d0);
   for (int e = threadIdx.x; e < nd * p.nsb; e += blockDim.x)
     s_tab[e] = p.tab[(int64_t)d0 * p.nsb + e];
@@ -177,11 +283,11 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_tree_stage2(const TreeS2 p) {
 
 template <int NSUB>
 cudaError_t launch_stage1(const TreeS1& a, int64_t tiles, int nsb, cudaStream_t st) {
-  const size_t smem = 2u * NSUB * tree_words(NSUB) * 4u;
+  const size_t smem = 2u * NSUB * tree_pitch(NSUB) * 4u;
   auto k = k_tree_stage1<NSUB>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<dim3((unsigned)tiles, (unsigned)nsb), kTreeThreads, smem, st>>>(a);
+  k<<<(unsigned)(tiles * nsb), kTreeThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -277,8 +383,8 @@ dd_status exec_tree(Plan& p, const ExecArgs& a) {
   s1.S = static_cast<uint32_t*>(p.d_tree_S.p);
   s1.s_pitch = pitch / 2;
   s1.roff = static_cast<const int32_t*>(p.d_tree_roff.p);
-  s1.len1 = len1;
   s1.nbits = a.in_nbits;
+  s1.nsb = nsb;
   {
     KernelTimer kt(&p, DD_KERNEL_DEDISP, a.st);
     if ((e = stage1(Np, s1, tiles, nsb, a.st)) != cudaSuccess) return cuda_status(e);
@@ -293,7 +399,7 @@ dd_status exec_tree(Plan& p, const ExecArgs& a) {
   s2.out = static_cast<uint32_t*>(a.out);
   s2.out_stride = a.out_stride;
   const int64_t t2 = (a.nsamps_out + 32 * kS2K - 1) / (32 * kS2K);
-  const dim3 grid((unsigned)t2, (unsigned)((n + kS2Warps - 1) / kS2Warps));
+  const unsigned grid = (unsigned)(t2 * ((n + kS2Warps - 1) / kS2Warps));
   const size_t smem = (size_t)kS2Warps * nsb * sizeof(int2);
   KernelTimer kt(&p, DD_KERNEL_STAGE2, a.st);
   k_tree_stage2<<<grid, kS2Warps * 32, smem, a.st>>>(s2);
