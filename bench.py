@@ -316,6 +316,17 @@ def run_serving(a):
                              dm_rule=dict(lo=c["dms"]["lo"], hi=c["dms"]["hi"],
                                           width_us=c["dms"]["width_us"], tol=c["dms"]["tol"])))
     gmax, gmin = c["gulp_hi"], c["gulp_lo"]
+    # the library's tiling search, once per band (on its first beam's plan),
+    # applied to every beam of that band; the batched launch runs one launch
+    # per tiling
+    tunings = {}
+    if not a.no_autotune:
+        for band in c["bands"]:
+            p0 = next(p for p in plans if p.nchans == band["nchans"])
+            p0.autotune(8, 1 << 17)
+            tunings[band["nchans"]] = p0.get_tuning()
+        for p in plans:
+            p.set_tuning(**tunings[p.nchans])
     host = {}
     for band in c["bands"]:
         nch = band["nchans"]
@@ -334,16 +345,33 @@ def run_serving(a):
     per_beam = 6
     cap_reqs = [(b, g) for g in sizes(per_beam) for b in range(len(plans))]
 
+    busy = {}
+
     def capacity(max_batch):
-        """Saturated throughput of the engine: every request queued at once."""
+        """Saturated throughput of the engine: every request queued at once;
+        also the share of the wall time the GPU spent in the transform's
+        kernels (the plans' own kernel timing)."""
         srv = dd.Server(arena_bytes=arena, max_batch=max_batch, max_inflight=2)
         beams = [srv.add_beam(p, 8, gmax) for p in plans]
         # warm-up: one full gulp per beam (stream images, staging tables)
         _serve_all(srv, plans, beams, [(b, gmax) for b in range(len(plans))], host)
+        for p in plans:
+            p.reset_kernel_timing()
+            p.set_kernel_timing(True)
         t0 = time.perf_counter()
         res = _serve_all(srv, plans, beams, cap_reqs, host)
         wall = time.perf_counter() - t0
         srv.close()
+        k_ms, n_launch = 0.0, 0
+        for p in plans:
+            p.set_kernel_timing(False)
+            for kind in (0, 1):
+                ms, n = p.kernel_timing(kind)
+                k_ms += ms
+                n_launch += n if kind == 1 else 0
+        busy[max_batch] = {"kernel_s": k_ms / 1e3, "wall_s": wall,
+                           "kernel_share_of_wall": k_ms / 1e3 / wall,
+                           "dedisp_launches": n_launch}
         return sum(u for _, u in res) / wall
 
     def sequential():
@@ -406,6 +434,8 @@ def run_serving(a):
         "capacity_sequential_per_beam": cap_s / 1e9,
         "batched_over_sequential": cap_b / cap_s,
         "capacity_requests": len(cap_reqs),
+        "gpu_busy": {"batched": busy.get(13), "one_beam_per_launch": busy.get(1)},
+        "tuning": {str(k): v for k, v in tunings.items()} or "per-format default",
         "unit": UNIT,
         "arena_gb": arena / 2**30,
         "latency_definition": "scheduled arrival -> output ready on the GPU (host-function "

@@ -269,7 +269,6 @@ static dd_status batch_launch(dd_batch b, void* cuda_stream, int64_t* nsamps_out
   if (!b || !nsamps_out) return DD_ERR_INVALID_ARG;
   if (b->items.empty()) return DD_OK;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  Plan& p0 = *b->items[0].stream->s.plan;
   const int nbits = b->items[0].stream->s.nbits;
   const int fmt = fmt_for_nbits(nbits);
   const size_t n = b->items.size();
@@ -292,21 +291,28 @@ static dd_status batch_launch(dd_batch b, void* cuda_stream, int64_t* nsamps_out
       job_item.push_back(i);
     }
   }
-  // The launches use the first plan's tiling; segments carry each beam's
-  // tables, and each trial block its own chunk size, so beams of any
-  // geometry share one persistent launch (per kMaxSegs beams).  Inside a
-  // launch, beams of the same shape (channels, trials) are kept adjacent in
-  // the work list: on the serving workload, interleaving 512- and
-  // 1024-channel beams made the launch 13-26 % slower than the same beams
-  // grouped.
+  // Beams run in one persistent launch per tiling: segments carry each
+  // beam's tables, and each trial block its own chunk size, so beams of any
+  // geometry share a launch (per kMaxSegs beams); beams whose plans were
+  // tuned differently (dd_plan_set_tuning, dd_plan_autotune) run in one
+  // launch per tiling, each with its own.  Inside a launch, beams of the
+  // same shape (channels, trials) are kept adjacent in the work list: on the
+  // serving workload, interleaving 512- and 1024-channel beams made the
+  // launch 13-26 % slower than the same beams grouped.
   {
     struct Key {
+      std::array<int, 3> tile;
       int nchans, ndm;
       size_t job;
     };
     std::vector<Key> key;
-    for (size_t k = 0; k < jobs.size(); ++k) key.push_back({jobs[k].nchans, jobs[k].ndm, k});
+    for (size_t k = 0; k < jobs.size(); ++k) {
+      const Tuning t = tuning_for(jobs[k].plan->tune, fmt);
+      key.push_back({{t.dms_per_block, t.words_per_lane, t.chans_per_chunk}, jobs[k].nchans,
+                     jobs[k].ndm, k});
+    }
     std::stable_sort(key.begin(), key.end(), [](const Key& a, const Key& b) {
+      if (a.tile != b.tile) return a.tile < b.tile;
       if (a.nchans != b.nchans) return a.nchans < b.nchans;
       return a.ndm < b.ndm;
     });
@@ -314,15 +320,17 @@ static dd_status batch_launch(dd_batch b, void* cuda_stream, int64_t* nsamps_out
     while (k0 < key.size()) {
       size_t k1 = k0;
       std::vector<DirectJob> part;
-      while (k1 < key.size() && part.size() < (size_t)kMaxSegs)
+      while (k1 < key.size() && part.size() < (size_t)kMaxSegs && key[k1].tile == key[k0].tile)
         part.push_back(jobs[key[k1++].job]);
+      // the launch takes the tiling (and status buffer) of its first beam's plan
+      Plan& pl = *const_cast<Plan*>(part[0].plan);
       LaunchPlan L;
       std::vector<std::shared_ptr<StageTab>> tabs;
-      dd_status r = plan_direct_launch(p0, fmt, fmt == FMT_F32 ? OUT_F32 : OUT_U32,
+      dd_status r = plan_direct_launch(pl, fmt, fmt == FMT_F32 ? OUT_F32 : OUT_U32,
                                        vmax_for_nbits(nbits), part, &L, &tabs);
       if (r != DD_OK) return r;
       if (hold) hold->insert(hold->end(), tabs.begin(), tabs.end());
-      if ((r = run_launch(p0, L, st)) != DD_OK) return r;
+      if ((r = run_launch(pl, L, st)) != DD_OK) return r;
       k0 = k1;
     }
   }

@@ -191,3 +191,35 @@ def test_batch_graph_needs_primed_streams():
     b.add(s, x, 1000, o)
     with pytest.raises(dd.DedispError):
         b.capture()                    # tail still empty
+
+
+def test_batch_of_differently_tuned_plans_equals_the_oracle(orc):
+    """Beams whose plans carry different tilings run in one launch per
+    tiling, each with its own; every beam's series is still exact."""
+    torch = torch_cuda()
+    plans = [_plan(256, 40, 400.0), _plan(128, 23, 300.0), _plan(256, 17, 250.0),
+             _plan(512, 31, 350.0)]
+    plans[0].set_tuning(64, 16, 2)
+    plans[1].set_tuning(16, 8, 4)
+    plans[3].set_tuning(32, 8, 8)
+    G, ngulps = 1500, 4
+    xs = [synth.uniform_packed(95 + i, 8, G * ngulps, p.nchans, 8) for i, p in enumerate(plans)]
+    streams = [dd.Stream(p, 8, G) for p in plans]
+    got = [[] for _ in plans]
+    for k in range(ngulps):
+        batch = dd.Batch()
+        bufs = []
+        for i, p in enumerate(plans):
+            x = torch.from_numpy(np.ascontiguousarray(xs[i][k * G:(k + 1) * G])).cuda()
+            o = torch.zeros((p.dm_count, G), dtype=torch.int32, device="cuda")
+            batch.add(streams[i], x, G, o)
+            bufs.append((x, o))
+        ks = batch.launch()
+        torch.cuda.synchronize()
+        for i in range(len(plans)):
+            got[i].append(bufs[i][1][:, :ks[i]].cpu().numpy().view(np.uint32))
+    for i, p in enumerate(plans):
+        series = np.concatenate(got[i], axis=1)
+        nout = G * ngulps - p.max_delay
+        assert series.shape[1] == nout
+        assert np.array_equal(series, orc.direct(xs[i], 8, p.nchans, nout, odelays(orc, p))), i
