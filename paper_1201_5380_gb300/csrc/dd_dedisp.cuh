@@ -32,6 +32,19 @@ template <> struct FmtT<FMT_BYTE> { static constexpr int SPW = 4, LW = 8; };
 template <> struct FmtT<FMT_HALF> { static constexpr int SPW = 2, LW = 16; };
 template <> struct FmtT<FMT_U32> { static constexpr int SPW = 1, LW = 32; };
 template <> struct FmtT<FMT_F32> { static constexpr int SPW = 1, LW = 32; };
+template <> struct FmtT<FMT_TRI> { static constexpr int SPW = 3, LW = 10; };
+
+// Word w of a staged row shifted by kap samples (the next word b supplies
+// the samples shifted in): a funnel shift for lanes that fill the word, an
+// explicit merge for the 10-bit lanes (bits 30-31 stay zero).
+template <int FMT>
+__device__ __forceinline__ uint32_t lane_shift(uint32_t a, uint32_t b, int kap) {
+  if constexpr (FMT == FMT_TRI) {
+    return kap == 1 ? (a >> 10) | ((b << 20) & 0x3FF00000u) : (a >> 20) | ((b << 10) & 0x3FFFFC00u);
+  } else {
+    return __funnelshift_r(a, b, kap * FmtT<FMT>::LW);
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Per-word accumulators.  flush0/1/2 move a level into the next wider one;
@@ -185,6 +198,45 @@ template <bool WIDE> struct Acc<FMT_U32, WIDE> {
   __device__ __forceinline__ void flush1() {}
   __device__ __forceinline__ void flush2() {}
   __device__ __forceinline__ void final(uint32_t v[1]) { v[0] = s; }
+};
+
+// 10-bit lanes: a word holds samples 0..2 in bits [0,10), [10,20),
+// [20,30).  Four channels of 8-bit samples fit a lane (4 * 255 < 1024), so
+// every group of four goes straight to three 32-bit sums: u0 and u2 take
+// lanes 0 and 2, u1 takes lane 1 in place (scaled by 2^10: the plan keeps
+// nchans * 255 * 2^10 below 2^32), which saves its shift.
+template <bool WIDE> struct Acc<FMT_TRI, WIDE> {
+  uint32_t t, u0, u1, u2;
+  __device__ __forceinline__ void zero() { t = u0 = u1 = u2 = 0u; }
+  __device__ __forceinline__ void add4(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
+    t = t + x0 + x1;
+    t = t + x2 + x3;
+  }
+  __device__ __forceinline__ void flush0() {
+    u0 += t & 0x3FFu;
+    u1 += t & 0xFFC00u;
+    u2 += t >> 20;
+    t = 0u;
+  }
+  // two groups of four channels, each summed in the 10-bit lanes, then
+  // widened together: one add per sum for both
+  __device__ __forceinline__ void add8_flush(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
+                                             uint32_t x4, uint32_t x5, uint32_t x6,
+                                             uint32_t x7) {
+    const uint32_t a = (x0 + x1) + (x2 + x3);
+    const uint32_t c = (x4 + x5) + (x6 + x7);
+    u0 += (a & 0x3FFu) + (c & 0x3FFu);
+    u1 += (a & 0xFFC00u) + (c & 0xFFC00u);
+    u2 += (a >> 20) + (c >> 20);
+  }
+  __device__ __forceinline__ void flush1() {}
+  __device__ __forceinline__ void flush2() {}
+  __device__ __forceinline__ void final(uint32_t v[3]) {
+    flush0();
+    v[0] = u0;
+    v[1] = u1 >> 10;
+    v[2] = u2;
+  }
 };
 
 // Float: channels are summed into a partial over 32 channels (8 groups),
@@ -512,10 +564,10 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
 #pragma unroll
           for (int kap = 1; kap < SPW; ++kap) {
             uint4 v;
-            v.x = __funnelshift_r(w.x, w.y, kap * LW);
-            v.y = __funnelshift_r(w.y, w.z, kap * LW);
-            v.z = __funnelshift_r(w.z, w.w, kap * LW);
-            v.w = __funnelshift_r(w.w, w4, kap * LW);
+            v.x = lane_shift<FMT>(w.x, w.y, kap);
+            v.y = lane_shift<FMT>(w.y, w.z, kap);
+            v.z = lane_shift<FMT>(w.z, w.w, kap);
+            v.w = lane_shift<FMT>(w.w, w4, kap);
             *reinterpret_cast<uint4*>(dst + (kap - 1) * nww) = v;
           }
         }
@@ -532,15 +584,17 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       bool paired = false;
       if constexpr (FMT == FMT_NIB)
         paired = p.f0 == 1 && p.f1 >= 2 && (cc & 7) == 0 && (cc >> 3) <= (p.f1 >> 1);
+      if constexpr (FMT == FMT_TRI) paired = (cc & 7) == 0;
       if (paired) {
         // 2-bit input: pairs of 4-channel groups widened together; a pair
         // adds at most two group sums to a byte lane, so byte lanes take
         // f1/2 pairs between 16-bit flushes.  The flush is taken before a
         // chunk whose pairs would pass that, so the pair loop itself has no
-        // branch.
-        if constexpr (FMT == FMT_NIB) {
+        // branch.  (8-bit input in 10-bit lanes widens every pair to 32
+        // bits: no flush between.)
+        if constexpr (FMT == FMT_NIB || FMT == FMT_TRI) {
           const int npairs = cc >> 3;
-          if (g1 + npairs > (p.f1 >> 1)) {
+          if (FMT == FMT_NIB && g1 + npairs > (p.f1 >> 1)) {
             g1 = 0;
 #pragma unroll
             for (int i = 0; i < DPW; ++i)
@@ -645,7 +699,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
                             ((int64_t)grp * S.g_out + (int64_t)(d0 + slot) * S.out_stride + tw) *
                                 esz;
           const bool full = p.vec_out && tw + SPW <= t_end;
-          if (esz == 2 && full && SPW >= 2) {
+          if (esz == 2 && full && (SPW == 2 || SPW == 4 || SPW == 8)) {
             uint32_t u[SPW / 2 > 0 ? SPW / 2 : 1];
 #pragma unroll
             for (int q = 0; q < SPW / 2; ++q) u[q] = w[2 * q] | (w[(2 * q + 1) % SPW] << 16);
@@ -656,7 +710,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
               *reinterpret_cast<uint2*>(row) = make_uint2(u[0], u[1 % (SPW / 2)]);
             else
               *reinterpret_cast<uint32_t*>(row) = u[0];
-          } else if (esz == 1 && full && SPW >= 4) {
+          } else if (esz == 1 && full && (SPW == 4 || SPW == 8)) {
             uint32_t u[SPW / 4 > 0 ? SPW / 4 : 1];
 #pragma unroll
             for (int q = 0; q < SPW / 4; ++q)

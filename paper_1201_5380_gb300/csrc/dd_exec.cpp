@@ -11,12 +11,12 @@
 
 namespace dd {
 
-int fmt_for_nbits(int nbits) {
+int fmt_for_nbits(int nbits, int nchans) {
   switch (nbits) {
     case 1:
     case 2: return FMT_NIB;
     case 4: return FMT_BYTE;
-    case 8: return FMT_HALF;
+    case 8: return (int64_t)nchans * 255 * 1024 < ((int64_t)1 << 32) ? FMT_TRI : FMT_HALF;
     case 32: return FMT_F32;
     default: return -1;
   }
@@ -125,6 +125,9 @@ static void flush_periods(int fmt, int vmax, int nchan_max, bool* wide, int* f0,
     case FMT_HALF:
       *f0 = std::max(1, 65535 / (4 * vmax));
       *wide = (int64_t)nchan_max * vmax > 65535;
+      break;
+    case FMT_TRI:
+      *f0 = 1;  // every group of 4 channels goes straight to 32-bit sums
       break;
     case FMT_F32:
       *f0 = 8;  // 32 channels per FP32 partial sum
@@ -254,7 +257,7 @@ static dd_status build_stage_tab(const TabSrc& src, int fmt, int cfg, int cc_cap
           const int d = std::min(d0 + i, d1 - 1);
           const int64_t o = (int64_t)kPad + dl[(int64_t)d * src.dstride + c] - woff * spw;
           const int64_t om = o / spw;
-          const int64_t kap = o & (spw - 1);
+          const int64_t kap = o % spw;
           // the unshifted copy is the landing window; copy kap >= 1 follows
           // the chunk's cc landing windows
           a[(int64_t)i * cc] =
@@ -534,7 +537,7 @@ static bool device_range_ok(const void* ptr, size_t bytes) {
 // needed, the job's image fields filled; nothing launched.
 static dd_status prepare_direct_image(Plan& p, int nbits, int64_t nsamps, DevBuf& image,
                                       DirectJob* j) {
-  const int fmt = fmt_for_nbits(nbits);
+  const int fmt = fmt_for_nbits(nbits, p.nchans);
   const int64_t rw = direct_row_words(p, fmt, nsamps);
   cudaError_t e = image.ensure((size_t)p.nchans * rw * 4);
   if (e != cudaSuccess) return cuda_status(e);
@@ -558,7 +561,8 @@ dd_status stage_direct_image(Plan& p, const void* in, int nbits, int64_t in_stri
   dd_status s = prepare_direct_image(p, nbits, nsamps, image, j);
   if (s != DD_OK) return s;
   KernelTimer kt(&p, 0, st);
-  return cuda_status(launch_corner_turn(nbits, static_cast<const uint8_t*>(in), in_stride, 0, rows,
+  return cuda_status(launch_corner_turn(nbits, fmt_for_nbits(nbits, p.nchans),
+                                        static_cast<const uint8_t*>(in), in_stride, 0, rows,
                                         p.nchans, static_cast<const uint8_t*>(p.d_mask.p),
                                         const_cast<uint32_t*>(j->img), j->row_words, 0,
                                         j->row_words, st));
@@ -657,7 +661,7 @@ static dd_status exec_direct_host_out(Plan& p, const ExecArgs& a, int fmt, const
       }
       {
         KernelTimer kt(&p, 0, a.st);
-        e = launch_corner_turn(a.in_nbits, d_in, a.in_row_stride, 0, rows, p.nchans,
+        e = launch_corner_turn(a.in_nbits, fmt, d_in, a.in_row_stride, 0, rows, p.nchans,
                                static_cast<const uint8_t*>(p.d_mask.p),
                                const_cast<uint32_t*>(j.img), rw, w_done, w_need, a.st);
       }
@@ -688,6 +692,9 @@ static dd_status exec_direct_host_out(Plan& p, const ExecArgs& a, int fmt, const
 
 static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
   if (fmt == FMT_F32) return DD_ERR_UNSUPPORTED_NBITS;
+  // stage 1 writes the intermediate in 16-bit lanes (OUT_HALFIMG) from an
+  // image of two samples a word: 8-bit input stays in 16-bit lanes here
+  if (fmt == FMT_TRI) fmt = FMT_HALF;
   dd_status s = upload_subband(p);
   if (s != DD_OK) return s;
   const int C = p.nchans, Np = p.sb_chans, nsb = C / Np;
@@ -711,7 +718,7 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
   const int64_t rows = G + p.sb_max_delay;
   {
     KernelTimer kt(&p, 0, a.st);
-    e = launch_corner_turn(a.in_nbits, static_cast<const uint8_t*>(a.in), a.in_row_stride, 0,
+    e = launch_corner_turn(a.in_nbits, fmt, static_cast<const uint8_t*>(a.in), a.in_row_stride, 0,
                            rows, C, static_cast<const uint8_t*>(p.d_mask.p), img, rw, 0, rw,
                            a.st);
   }
@@ -808,7 +815,7 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
 }
 
 dd_status exec_device(Plan& p, const ExecArgs& a) {
-  const int fmt = fmt_for_nbits(a.in_nbits);
+  const int fmt = fmt_for_nbits(a.in_nbits, p.nchans);
   if (fmt < 0) return DD_ERR_UNSUPPORTED_NBITS;
   dd_status s = ensure_device_tables(p);
   if (s != DD_OK) return s;
@@ -825,7 +832,7 @@ extern "C" dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void* in
                                 void* cuda_stream, unsigned flags) {
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (!p || !in || !out || nsamps_out <= 0 || out_stride < nsamps_out) return DD_ERR_INVALID_ARG;
-  const int fmt = fmt_for_nbits(in_nbits);
+  const int fmt = fmt_for_nbits(in_nbits, p->nchans);
   if (fmt < 0) return DD_ERR_UNSUPPORTED_NBITS;
   if (p->dms.empty()) return DD_ERR_NO_DM_LIST;
   const int64_t row_bytes =
@@ -908,7 +915,7 @@ extern "C" dd_status dd_plan_get_chunk_geometry(dd_plan plan, int in_nbits, int3
                                                size_t* smem_bytes) {
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (!p || !n_blocks) return DD_ERR_INVALID_ARG;
-  const int fmt = fmt_for_nbits(in_nbits);
+  const int fmt = fmt_for_nbits(in_nbits, p->nchans);
   if (fmt < 0) return DD_ERR_UNSUPPORTED_NBITS;
   if (p->dms.empty()) return DD_ERR_NO_DM_LIST;
   std::lock_guard<std::mutex> lk(p->mu);

@@ -28,8 +28,10 @@ namespace dd {
 //   FMT_HALF 16-bit lanes, 2 samples/word, 8-bit input and sub-band stage 2
 //   FMT_U32  32-bit unsigned, 1 sample/word, wide sub-band intermediates
 //   FMT_F32  32-bit float, 1 sample/word, float input
+//   FMT_TRI  10-bit lanes at bits [0,10), [10,20), [20,30), 3 samples/word,
+//            8-bit input of the direct transform (4 channels fit a lane)
 // ---------------------------------------------------------------------------
-enum Fmt { FMT_NIB = 0, FMT_BYTE = 1, FMT_HALF = 2, FMT_U32 = 3, FMT_F32 = 4 };
+enum Fmt { FMT_NIB = 0, FMT_BYTE = 1, FMT_HALF = 2, FMT_U32 = 3, FMT_F32 = 4, FMT_TRI = 5 };
 // OUT_NARROW: scaled uint8/uint16 rows (LaunchParams::out_bits, out_shift),
 // a separate instantiation so the uint32 kernel's code is untouched.
 enum OutKind { OUT_U32 = 0, OUT_F32 = 1, OUT_HALFIMG = 2, OUT_NARROW = 3 };
@@ -41,10 +43,10 @@ inline int fmt_spw(int fmt) {
     case FMT_NIB: return 8;
     case FMT_BYTE: return 4;
     case FMT_HALF: return 2;
+    case FMT_TRI: return 3;
     default: return 1;
   }
 }
-inline int fmt_lane_bits(int fmt) { return 32 / fmt_spw(fmt); }
 
 // Device status flags (OR-ed by kernels, read by dd_plan_get_device_status).
 enum : uint32_t {
@@ -138,8 +140,9 @@ cudaError_t launch_dedisp(int fmt, int outk, bool wide, int cfg, const LaunchPar
                           int grid, size_t smem, cudaStream_t st);
 cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, bool pbg, size_t smem,
                                      int* nblk);
-// Image words [w_first, words) of every channel row.
-cudaError_t launch_corner_turn(int nbits, const uint8_t* in, int64_t in_stride,
+// Image words [w_first, words) of every channel row, in staged format fmt
+// (fmt_for_nbits, or FMT_HALF for 8-bit input of the sub-band method).
+cudaError_t launch_corner_turn(int nbits, int fmt, const uint8_t* in, int64_t in_stride,
                                int64_t t_begin, int64_t nrows_valid, int nchans,
                                const uint8_t* mask, uint32_t* img, int64_t row_words,
                                int64_t w_first, int64_t words, cudaStream_t st);
@@ -387,7 +390,11 @@ dd_status stage_direct_image(Plan& p, const void* in, int nbits, int64_t in_stri
                              int64_t nsamps, DevBuf& image, cudaStream_t st, DirectJob* j);
 
 dd_status cuda_status(cudaError_t e);
-int fmt_for_nbits(int nbits);
+// Staged format of the direct transform for nbits input over nchans
+// channels (-1: unsupported nbits).  8-bit input takes 10-bit lanes, three
+// samples a word, while the middle lane's in-place sums fit 32 bits
+// (nchans * 255 * 2^10 < 2^32), else 16-bit lanes.
+int fmt_for_nbits(int nbits, int nchans);
 int vmax_for_nbits(int nbits);
 
 }  // namespace dd

@@ -15,6 +15,8 @@ cudaError_t dispatch_half(int, bool, int, bool, const LaunchParams*, int, size_t
                           int*);
 cudaError_t dispatch_word(int, int, bool, int, bool, const LaunchParams*, int, size_t,
                           cudaStream_t, int*);
+cudaError_t dispatch_tri(int, bool, int, bool, const LaunchParams*, int, size_t, cudaStream_t,
+                         int*);
 
 static cudaError_t dispatch(int fmt, int outk, bool wide, int cfg, bool pbg,
                             const LaunchParams* p, int grid, size_t smem, cudaStream_t st,
@@ -23,6 +25,7 @@ static cudaError_t dispatch(int fmt, int outk, bool wide, int cfg, bool pbg,
     case FMT_NIB: return dispatch_nib(outk, wide, cfg, pbg, p, grid, smem, st, occ);
     case FMT_BYTE: return dispatch_byte(outk, wide, cfg, pbg, p, grid, smem, st, occ);
     case FMT_HALF: return dispatch_half(outk, wide, cfg, pbg, p, grid, smem, st, occ);
+    case FMT_TRI: return dispatch_tri(outk, wide, cfg, pbg, p, grid, smem, st, occ);
     default: return dispatch_word(fmt, outk, wide, cfg, pbg, p, grid, smem, st, occ);
   }
 }
@@ -60,7 +63,7 @@ size_t dedisp_smem_bytes(int fmt, int cfg, int cc, int nww) {
 // into shared memory with coalesced byte loads; phase 2 builds image words,
 // consecutive threads writing consecutive words of one channel row.
 // ---------------------------------------------------------------------------
-template <int NBITS>
+template <int NBITS, int FMT>
 __global__ void __launch_bounds__(256) k_corner_turn(const uint8_t* __restrict__ in,
                                                      int64_t in_stride, int64_t t_begin,
                                                      int64_t nrows_valid, int nchans,
@@ -69,8 +72,8 @@ __global__ void __launch_bounds__(256) k_corner_turn(const uint8_t* __restrict__
                                                      int64_t row_words, int64_t w_first,
                                                      int64_t words) {
   constexpr bool F32 = (NBITS == 32);
-  constexpr int SPW = F32 ? 1 : (NBITS <= 2 ? 8 : (NBITS == 4 ? 4 : 2));
-  constexpr int LW = 32 / SPW;
+  constexpr int SPW = FMT == FMT_TRI ? 3 : (F32 ? 1 : (NBITS <= 2 ? 8 : (NBITS == 4 ? 4 : 2)));
+  constexpr int LW = FMT == FMT_TRI ? 10 : 32 / SPW;
   constexpr int ROWB = F32 ? 128 : 32;           // raw bytes per row in the block
   constexpr int CB = F32 ? 32 : 256 / NBITS;     // channels per block
   constexpr int WB = F32 ? 64 : 32;              // image words per block
@@ -230,12 +233,68 @@ __global__ void __launch_bounds__(256) k_corner_turn_8bit(const uint8_t* __restr
   }
 }
 
-cudaError_t launch_corner_turn(int nbits, const uint8_t* in, int64_t in_stride, int64_t t_begin,
-                               int64_t nrows_valid, int nchans, const uint8_t* mask,
-                               uint32_t* img, int64_t row_words, int64_t w_first, int64_t words,
-                               cudaStream_t st) {
+// 8-bit input into 10-bit lanes (three samples a word), 16-byte-aligned
+// rows: the serving bands, specialised like the kernel above.  Block = 256
+// threads over 64 channels x 64 image words (192 rows).  Phase 1 stores the
+// rows' bytes channel major; phase 2: a thread reads 12 samples of a
+// channel with three 32-bit loads and writes the 4 image words they make
+// with one 16-byte store.  Requires in, in_stride 16-byte aligned, nchans %
+// 64 == 0, row_words, w_first and words multiples of 4.
+__global__ void __launch_bounds__(256) k_corner_turn_8bit_tri(const uint8_t* __restrict__ in,
+                                                              int64_t in_stride, int64_t t_begin,
+                                                              int64_t nrows_valid,
+                                                              const uint8_t* __restrict__ mask,
+                                                              uint32_t* __restrict__ img,
+                                                              int64_t row_words, int64_t w_first,
+                                                              int64_t words) {
+  constexpr int ROWS = 192, CH = 64, PITCH = ROWS + 8;  // bytes per channel row of the tile
+  __shared__ __align__(16) uint8_t tile[CH * PITCH];
+  const int64_t w0 = w_first + (int64_t)blockIdx.x * 64;  // first image word
+  const int cb0 = blockIdx.y * CH;                        // first channel
+  const int64_t r0 = t_begin + w0 * 3 - kPad;             // raw row of the block's first sample
+  for (int e = threadIdx.x; e < ROWS * 4; e += 256) {
+    const int rr = e % ROWS;
+    const int pc = e / ROWS;  // 16-channel piece of the row
+    const int64_t r = r0 + rr;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (r >= t_begin && r < t_begin + nrows_valid)
+      v = __ldg(reinterpret_cast<const uint4*>(in + r * in_stride + cb0 + 16 * pc));
+    const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        tile[(16 * pc + 4 * q + k) * PITCH + rr] = (uint8_t)(x[q] >> (8 * k));
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < CH * 16; e += 256) {
+    const int cl = e >> 4;
+    const int qd = e & 15;
+    const int64_t w = w0 + 4 * qd;
+    if (w >= words) continue;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&tile[cl * PITCH + 12 * qd]);
+    const uint32_t a = src[0], b = src[1], c = src[2];  // samples 0-3, 4-7, 8-11
+    // samples 3i, 3i+1, 3i+2 into the 10-bit lanes of word i
+    auto s = [&](int k) -> uint32_t {
+      const uint32_t x = k < 4 ? a : (k < 8 ? b : c);
+      return (x >> (8 * (k & 3))) & 0xFFu;
+    };
+    uint4 o = make_uint4(s(0) | (s(1) << 10) | (s(2) << 20), s(3) | (s(4) << 10) | (s(5) << 20),
+                         s(6) | (s(7) << 10) | (s(8) << 20), s(9) | (s(10) << 10) | (s(11) << 20));
+    const int ch = cb0 + cl;
+    if (mask && mask[ch] == 0) o = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(img + (int64_t)ch * row_words + w) = o;
+  }
+}
+
+cudaError_t launch_corner_turn(int nbits, int fmt, const uint8_t* in, int64_t in_stride,
+                               int64_t t_begin, int64_t nrows_valid, int nchans,
+                               const uint8_t* mask, uint32_t* img, int64_t row_words,
+                               int64_t w_first, int64_t words, cudaStream_t st) {
   const int CB = nbits == 32 ? 32 : 256 / nbits;
   const int WB = nbits == 32 ? 64 : 32;
+  const bool tri = fmt == FMT_TRI;
+  if (tri && nbits != 8) return cudaErrorInvalidValue;
   if (w_first < 0 || w_first >= words) return cudaSuccess;
   const int64_t n = words - w_first;
   dim3 grid((unsigned)((n + WB - 1) / WB), (unsigned)((nchans + CB - 1) / CB));
@@ -252,16 +311,26 @@ cudaError_t launch_corner_turn(int nbits, const uint8_t* in, int64_t in_stride, 
       !(in_stride & 15) && !(row_words & 3) && !(w_first & 3) && !(words & 3) &&
       !(reinterpret_cast<uintptr_t>(img) & 15)) {
     const dim3 g8((unsigned)((n + 63) / 64), (unsigned)(nchans / 64));
-    k_corner_turn_8bit<<<g8, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, mask, img,
-                                           row_words, w_first, words);
+    if (tri)
+      k_corner_turn_8bit_tri<<<g8, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, mask, img,
+                                                 row_words, w_first, words);
+    else
+      k_corner_turn_8bit<<<g8, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, mask, img,
+                                             row_words, w_first, words);
+    return cudaGetLastError();
+  }
+  if (tri) {
+    // the generic kernel's block covers 32 image words: 96 rows for 3 samples a word
+    k_corner_turn<8, FMT_TRI><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans,
+                                                    mask, img, row_words, w_first, words);
     return cudaGetLastError();
   }
   switch (nbits) {
-    case 1: k_corner_turn<1><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
-    case 2: k_corner_turn<2><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
-    case 4: k_corner_turn<4><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
-    case 8: k_corner_turn<8><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
-    case 32: k_corner_turn<32><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
+    case 1: k_corner_turn<1, FMT_NIB><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
+    case 2: k_corner_turn<2, FMT_NIB><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
+    case 4: k_corner_turn<4, FMT_BYTE><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
+    case 8: k_corner_turn<8, FMT_HALF><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
+    case 32: k_corner_turn<32, FMT_F32><<<grid, 256, 0, st>>>(in, in_stride, t_begin, nrows_valid, nchans, mask, img, row_words, w_first, words); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -54,7 +54,7 @@ extern "C" dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const 
                                         int64_t out_stride, void* cuda_stream) {
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (!p || !in || !out || nsamps_out <= 0 || out_stride < nsamps_out) return DD_ERR_INVALID_ARG;
-  const int fmt = fmt_for_nbits(in_nbits);
+  const int fmt = fmt_for_nbits(in_nbits, p->nchans);
   if (fmt < 0) return DD_ERR_UNSUPPORTED_NBITS;
   if (p->dms.empty()) return DD_ERR_NO_DM_LIST;
   if (p->out_bits != 32) return DD_ERR_INVALID_ARG;
@@ -129,7 +129,7 @@ extern "C" dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const 
   if (e != cudaSuccess) return cuda_status(e);
 
   const int64_t rows = nsamps_out + p->max_delay;
-  e = launch_corner_turn(in_nbits, static_cast<const uint8_t*>(in), in_row_stride, 0, rows,
+  e = launch_corner_turn(in_nbits, fmt, static_cast<const uint8_t*>(in), in_row_stride, 0, rows,
                          p->nchans, mask, img, rw, 0, rw, st);
   if (e != cudaSuccess) return cuda_status(e);
 

@@ -294,7 +294,7 @@ static bool have_cfg(int B, int K) {
 Tuning tuning_for(const Tuning& t, int fmt) {
   if (t.words_per_lane > 0) return t;
   Tuning r = t;
-  const bool narrow = fmt == FMT_HALF || fmt == FMT_U32 || fmt == FMT_F32;
+  const bool narrow = fmt == FMT_HALF || fmt == FMT_U32 || fmt == FMT_F32 || fmt == FMT_TRI;
   const int prefs[3] = {narrow ? 8 : 4, 4, 2};
   for (int k : prefs)
     if (have_cfg(t.dms_per_block, k)) {

@@ -101,7 +101,7 @@ dd_status dd_stream_create(dd_stream* out, dd_plan plan, int nbits, int64_t max_
   *out = nullptr;
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (!p || max_gulp <= 0) return DD_ERR_INVALID_ARG;
-  if (fmt_for_nbits(nbits) < 0) return DD_ERR_UNSUPPORTED_NBITS;
+  if (fmt_for_nbits(nbits, p->nchans) < 0) return DD_ERR_UNSUPPORTED_NBITS;
   if (p->dms.empty()) return DD_ERR_NO_DM_LIST;
   if (p->out_bits != 32) return DD_ERR_INVALID_ARG;  // streams write uint32 rows
   dd_stream h = new (std::nothrow) dd_stream_s();
@@ -140,7 +140,7 @@ dd_status dd_stream_push(dd_stream h, const void* in, int64_t n_in, int64_t in_s
   if (r != DD_OK) return r;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const bool device = (flags & DD_DEVICE_PTRS) != 0;
-  const int fmt = fmt_for_nbits(s.nbits);
+  const int fmt = fmt_for_nbits(s.nbits, p.nchans);
   DirectJob job;
   int64_t n_out = 0, total = 0;
   if ((r = stream_stage(s, in, n_in, in_stride, device, st, &job, &n_out, &total)) != DD_OK)
@@ -270,7 +270,9 @@ static dd_status batch_launch(dd_batch b, void* cuda_stream, int64_t* nsamps_out
   if (b->items.empty()) return DD_OK;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int nbits = b->items[0].stream->s.nbits;
-  const int fmt = fmt_for_nbits(nbits);
+  int nchans_max = 0;
+  for (const BatchItem& it : b->items) nchans_max = std::max(nchans_max, it.stream->s.plan->nchans);
+  const int fmt = fmt_for_nbits(nbits, nchans_max);
   const size_t n = b->items.size();
   std::vector<int64_t> totals(n, 0), nouts(n, 0);
   std::vector<DirectJob> jobs;
@@ -453,7 +455,7 @@ void dd_batch_graph_destroy(dd_batch_graph g) { delete g; }
 dd_status dd_plan_autotune(dd_plan plan, int nbits, int64_t nsamps, void* cuda_stream) {
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (!p || nsamps <= 0) return DD_ERR_INVALID_ARG;
-  if (fmt_for_nbits(nbits) < 0) return DD_ERR_UNSUPPORTED_NBITS;
+  if (fmt_for_nbits(nbits, p->nchans) < 0) return DD_ERR_UNSUPPORTED_NBITS;
   if (p->dms.empty()) return DD_ERR_NO_DM_LIST;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int64_t rb = input_row_bytes(p->nchans, nbits);

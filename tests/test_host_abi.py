@@ -198,20 +198,21 @@ def test_chunk_geometry_per_trial_block():
     assert max(p.chunk_geometry(2)["chans_per_chunk"]) <= 16
     # a small band with one narrow window everywhere: one geometry
     t = dd.Plan(64, 64e-6, 1500.0, -1.0, dms=[float(i) for i in range(101)])
-    gt = t.chunk_geometry(8)
+    gt = t.chunk_geometry(2)
     assert len(set(gt["chans_per_chunk"].tolist())) == 1
     assert len(set(gt["window_words"].tolist())) == 1
 
 
 def test_chunk_geometry_8bit_wide_trials():
-    """8-bit input keeps two samples per word, so the highest trials' windows
-    (to DM 2000) leave room for only 4 channels, the lowest for 32."""
+    """8-bit input keeps three samples per word (and two shifted copies), so
+    the highest trials' windows (to DM 2000) leave room for only 4 channels
+    per chunk, the lowest for 16."""
     from synth import configs
     c = configs.SURVEY
     p = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=2000.0))
     g = p.chunk_geometry(8)
     cc = g["chans_per_chunk"]
-    assert cc[0] == 32 and cc[int(np.argmax(g["window_words"]))] == 4 and cc.min() == 4
+    assert cc[0] == 16 and cc[int(np.argmax(g["window_words"]))] == 4 and cc.min() == 4
     with pytest.raises(dd.DedispError):
         p.chunk_geometry(3)
 
