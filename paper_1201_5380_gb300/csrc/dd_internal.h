@@ -291,6 +291,7 @@ dd_status ensure_device_tables(Plan& p);
 dd_status prepare_subband(Plan& p);  // host tables only
 dd_status upload_subband(Plan& p);   // host tables + device copies
 int tile_cfg_index(const Tuning& t);
+bool have_tile_cfg(int dms_per_block, int words_per_lane);  // a compiled shape
 // The tuning a launch of staged format fmt uses: words per lane 0 resolves
 // to 8 for the narrow-accumulator formats (16- and 32-bit lanes: 8-bit and
 // float input, the sub-band intermediate) and 4 otherwise, when a compiled

@@ -285,7 +285,7 @@ dd_status upload_subband(Plan& p) {
   return DD_OK;
 }
 
-static bool have_cfg(int B, int K) {
+bool have_tile_cfg(int B, int K) {
   for (int i = 0; i < kNumTileCfgs; ++i)
     if (kTileCfgs[i].nwarp * kTileCfgs[i].dpw == B && kTileCfgs[i].k == K) return true;
   return false;
@@ -297,7 +297,7 @@ Tuning tuning_for(const Tuning& t, int fmt) {
   const bool narrow = fmt == FMT_HALF || fmt == FMT_U32 || fmt == FMT_F32 || fmt == FMT_TRI;
   const int prefs[3] = {narrow ? 8 : 4, 4, 2};
   for (int k : prefs)
-    if (have_cfg(t.dms_per_block, k)) {
+    if (have_tile_cfg(t.dms_per_block, k)) {
       r.words_per_lane = k;
       return r;
     }
