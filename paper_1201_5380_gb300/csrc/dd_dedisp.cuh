@@ -585,7 +585,11 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       if constexpr (FMT == FMT_NIB)
         paired = p.f0 == 1 && p.f1 >= 2 && (cc & 7) == 0 && (cc >> 3) <= (p.f1 >> 1);
       if constexpr (FMT == FMT_TRI) paired = (cc & 7) == 0;
-      if (paired) {
+      if (warp * DPW >= nd) {
+        // every trial slot of this warp is past the block's last trial: its
+        // sums would be discarded (a short last block, a short sub-band
+        // group), so the warp only stages
+      } else if (paired) {
         // 2-bit input: pairs of 4-channel groups widened together; a pair
         // adds at most two group sums to a byte lane, so byte lanes take
         // f1/2 pairs between 16-bit flushes.  The flush is taken before a

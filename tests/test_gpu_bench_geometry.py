@@ -136,3 +136,53 @@ def test_server_on_the_serving_bands(orc):
         ref = orc.direct(xs[b], 8, p.nchans, nout, odelays(orc, p))
         assert np.array_equal(series, ref), b
     server.close()
+
+
+def _sample_points(rng, ndm, G, n=3000):
+    ds = rng.integers(0, ndm, n)
+    ts = rng.integers(0, G, n)
+    # every trial at the last sample, and the last samples of the last trial
+    ds = np.concatenate([ds, np.arange(ndm), np.full(8, ndm - 1)])
+    ts = np.concatenate([ts, np.full(ndm, G - 1), np.arange(G - 8, G)])
+    return ds, ts
+
+
+@pytest.mark.parametrize("tiling", ["default", "autotune"])
+def test_8bit_dm2000_full_gulp_sampled(orc, tiling):
+    """The benchmark's 8-bit line at its full size: 1024 channels, DM 0-2000
+    (1434 trials), 2^19 samples, in the default tiling and the autotuner's;
+    sampled points (random, every trial's last sample, the last row's tail)
+    against the oracle's Eq. 2 at those points."""
+    torch = torch_cuda()
+    plan = _plan(1024, SURVEY["df"], 2000.0)
+    if tiling == "autotune":
+        plan.autotune(8, 1 << 17)
+    G = 1 << 19
+    x = _input(8, 1024, G + plan.max_delay, 170)
+    d_in = torch.from_numpy(x).cuda()
+    out = torch.empty((plan.dm_count, G), dtype=torch.int32, device="cuda")
+    plan.execute(d_in, 8, G, out)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    ds, ts = _sample_points(np.random.default_rng(17), plan.dm_count, G)
+    got = out[torch.from_numpy(ds).cuda(), torch.from_numpy(ts).cuda()].cpu().numpy().view(np.uint32)
+    from _gpu import odelays
+    assert np.array_equal(got, orc.direct_points(x, 8, 1024, odelays(orc, plan), ds, ts))
+
+
+def test_float_dm2000_full_gulp_sampled(orc):
+    """Float input at the format sweep's 2^17 gulp, DM 0-2000: sampled points
+    within 1e-5 * sum_c |A| of the FP64 oracle."""
+    torch = torch_cuda()
+    plan = _plan(1024, SURVEY["df"], 2000.0)
+    G = 1 << 17
+    x = _input(32, 1024, G + plan.max_delay, 171)
+    d_in = torch.from_numpy(x).cuda()
+    out = torch.empty((plan.dm_count, G), dtype=torch.float32, device="cuda")
+    plan.execute(d_in, 32, G, out)
+    torch.cuda.synchronize()
+    ds, ts = _sample_points(np.random.default_rng(18), plan.dm_count, G)
+    got = out[torch.from_numpy(ds).cuda(), torch.from_numpy(ts).cuda()].cpu().numpy()
+    from _gpu import odelays
+    ref, ab = orc.direct_points_f32(x, odelays(orc, plan), ds, ts)
+    assert np.all(np.abs(got.astype(np.float64) - ref) <= F32_TOL * ab)
