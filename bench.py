@@ -838,6 +838,8 @@ def profile_step(a, plan, x, G, dev):
         p = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dms=dms)
         p.set_tree(32)
         rows, kw = p.input_rows(G, tree=True), dict(tree=True)
+    if a.tiling:
+        p.set_tuning(*[int(v) for v in a.tiling.split(",")])
     xx = np.ascontiguousarray(x[:rows]) if x.shape[0] >= rows else np.concatenate(
         [x, np.zeros((rows - x.shape[0],) + x.shape[1:], x.dtype)])
     d_in = torch.from_numpy(xx).to(dev)
@@ -854,6 +856,7 @@ def profile_step(a, plan, x, G, dev):
     k1, n1 = p.kernel_timing(1)
     k2, n2 = p.kernel_timing(2)
     print(json.dumps({"profile_step": a.profile_step, "gulp": G, "ndm": p.dm_count,
+                      "tuning": p.get_tuning(),
                       "stage1_ms": k1 / max(n1, 1), "stage2_ms": k2 / max(n2, 1),
                       "status": p.device_status()}))
     return 0

@@ -192,12 +192,16 @@ dd_status dd_plan_get_input_rows(dd_plan plan, int64_t nsamps_out, unsigned flag
 /* Kernel tiling: trials per thread block (16, 32 or 64), the most channels
  * staged per pass (4, 8, 16 or 32; default 32: each trial block stages as
  * many as its windows leave room for in shared memory) and output words per
- * lane (2, 4 or 8; compiled
- * shapes: 32x4, 64x2, 16x4, 32x2, 32x8 trials x words).  0 keeps the current
- * value.  words_per_lane < 0 (the default) picks it per input format: 8 for
- * 8-bit and float input (16- and 32-bit lanes), 4 for 1/2/4-bit input.
- * The autotuner below sets all three.  dd_plan_get_tuning reports 0 words
- * per lane while it is chosen per format. */
+ * lane (2, 4, 8 or 16; compiled shapes: 32x4, 64x2, 16x4, 32x2, 32x8 and
+ * 32x16 trials x words, the last only where the staged image holds one or
+ * two samples a word: float input and the sub-band method's second stage;
+ * an execute whose staged format lacks the shape returns DD_ERR_INVALID_ARG).  0
+ * keeps the current value.  words_per_lane < 0 (the default) picks it per
+ * staged format: 16 for one or two samples a word (float input, 16-bit
+ * lanes), 8 for 8-bit input (three samples a word), 4 for 1/2/4-bit input.
+ * The autotuner below sets all three for the format it is given.
+ * dd_plan_get_tuning reports 0 words per lane while it is chosen per
+ * format. */
 dd_status dd_plan_set_tuning(dd_plan plan, int dms_per_block, int chans_per_chunk,
                              int words_per_lane);
 dd_status dd_plan_get_tuning(dd_plan plan, int *dms_per_block, int *chans_per_chunk,

@@ -797,6 +797,15 @@ cudaError_t dispatch_cfg(int cfg, bool pbg, const LaunchParams* p, int grid, siz
     DD_CFG_CASE(2)
     DD_CFG_CASE(3)
     DD_CFG_CASE(4)
+    case 5:
+      // 16 words a lane: only where a word's accumulators take one or two
+      // registers (the other formats would spill)
+      if constexpr (FmtT<FMT>::SPW <= 2) {
+        return pbg ? run_one<FMT, OUTK, WIDE, 16, 2, 16, true>(p, grid, smem, st, occ)
+                   : run_one<FMT, OUTK, WIDE, 16, 2, 16, false>(p, grid, smem, st, occ);
+      } else {
+        return cudaErrorInvalidValue;
+      }
 #undef DD_CFG_CASE
     default:
       return cudaErrorInvalidValue;

@@ -340,6 +340,8 @@ static dd_status finish_launch(Plan& p, const Tuning& tune, int fmt, int outk, i
   const int cfg = tile_cfg_index(tune);
   const int B = kTileCfgs[cfg].nwarp * kTileCfgs[cfg].dpw;
   const int T = time_tile(fmt, tune);
+  // 16 words a lane is compiled only for one or two samples a word
+  if (kTileCfgs[cfg].k > 8 && fmt_spw(fmt) > 2) return DD_ERR_INVALID_ARG;
   int nchan_max = 0;
   for (auto& s : specs) nchan_max = std::max(nchan_max, (int)s.seg.nchan);
   // largest channels per chunk (the staging tables pick each block's own)

@@ -131,9 +131,13 @@ struct TileCfg {
 };
 // (16, 2, 8) is for the narrow-accumulator formats (8-bit and wider input,
 // where a wide window over a short tile makes staging dominate); the 4- and
-// 8-bit-lane formats compile it too but spill.
-constexpr TileCfg kTileCfgs[] = {{16, 2, 4}, {16, 4, 2}, {8, 2, 4}, {8, 4, 2}, {16, 2, 8}};
-constexpr int kNumTileCfgs = 5;
+// 8-bit-lane formats compile it too but spill.  (16, 2, 16) is compiled only
+// for the one- and two-sample-a-word formats (16-bit lanes, 32-bit words),
+// whose accumulators take one or two registers a word: short work items
+// (the sub-band method's second stage) gain most from its longer tiles.
+constexpr TileCfg kTileCfgs[] = {{16, 2, 4}, {16, 4, 2}, {8, 2, 4}, {8, 4, 2}, {16, 2, 8},
+                                 {16, 2, 16}};
+constexpr int kNumTileCfgs = 6;
 
 // Host launchers (dd_kernels_*.cu).
 cudaError_t launch_dedisp(int fmt, int outk, bool wide, int cfg, const LaunchParams& p,

@@ -294,8 +294,11 @@ bool have_tile_cfg(int B, int K) {
 Tuning tuning_for(const Tuning& t, int fmt) {
   if (t.words_per_lane > 0) return t;
   Tuning r = t;
-  const bool narrow = fmt == FMT_HALF || fmt == FMT_U32 || fmt == FMT_F32 || fmt == FMT_TRI;
-  const int prefs[3] = {narrow ? 8 : 4, 4, 2};
+  // words per lane by accumulator width: 16 where a word's sums take one or
+  // two registers (16-bit lanes, 32-bit words), 8 for the 10-bit lanes'
+  // three, 4 for the 4- and 8-bit lanes
+  const bool one_two = fmt == FMT_HALF || fmt == FMT_U32 || fmt == FMT_F32;
+  const int prefs[4] = {one_two ? 16 : (fmt == FMT_TRI ? 8 : 4), one_two ? 8 : 4, 4, 2};
   for (int k : prefs)
     if (have_tile_cfg(t.dms_per_block, k)) {
       r.words_per_lane = k;
