@@ -299,3 +299,22 @@ def test_8bit_lane_sums_at_the_channel_limit(orc, nchans):
     x = synth.uniform_packed(60, 8, rows, nchans, 8)
     got, _ = run_direct(plan, x, 8, nsamps)
     assert np.array_equal(got, orc.direct(x, 8, nchans, nsamps, odelays(orc, plan)))
+
+
+def test_sixteen_word_tile_only_for_one_or_two_samples_a_word(orc):
+    """32 trials x 16 words a lane is compiled for float input and 16-bit
+    lanes only: with it, float input stays within tolerance and 2-bit input
+    is refused before any launch."""
+    torch_cuda()
+    plan = _survey_plan(hi=2000.0, step=30)
+    plan.set_tuning(32, 32, 16)
+    nsamps = 1500
+    rows = nsamps + plan.max_delay
+    xf = synth.normal_f32(40, 0, rows, 1024)
+    got, _ = run_direct(plan, xf, 32, nsamps)
+    ref, ab = orc.direct_f32(xf, nsamps, odelays(orc, plan))
+    assert np.all(np.abs(got.astype(np.float64) - ref) <= F32_TOL * ab)
+    x2 = synth.uniform_packed(41, 0, rows, 1024, 2)
+    with pytest.raises(dd.DedispError) as e:
+        run_direct(plan, x2, 2, nsamps)
+    assert e.value.code == 1
