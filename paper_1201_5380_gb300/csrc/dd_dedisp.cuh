@@ -74,14 +74,19 @@ template <bool WIDE> struct Acc<FMT_NIB, WIDE> {
   }
   // Two groups of four channels whose 4-bit sums each fit a nibble (f0 ==
   // 1), widened to the 8-bit lanes together: one add per lane set for both.
+  // The odd nibbles are not masked here: b1 takes the plain sum of a >> 4,
+  // which is the odd nibbles in their byte lanes plus the even nibbles of
+  // bytes 1..3 four bits up, i.e. b1 + ((b0 & 0xFFFFFF00) >> 4) (mod 2^32);
+  // pair_fix() takes the second part back out before a flush.
   __device__ __forceinline__ void add8_flush(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
                                              uint32_t x4, uint32_t x5, uint32_t x6,
                                              uint32_t x7) {
     const uint32_t a = (x0 + x1) + (x2 + x3);
     const uint32_t c = (x4 + x5) + (x6 + x7);
     b0 += (a & 0x0F0F0F0Fu) + (c & 0x0F0F0F0Fu);
-    b1 += ((a >> 4) & 0x0F0F0F0Fu) + ((c >> 4) & 0x0F0F0F0Fu);
+    b1 += (a >> 4) + (c >> 4);
   }
+  __device__ __forceinline__ void pair_fix() { b1 -= (b0 & 0xFFFFFF00u) >> 4; }
   __device__ __forceinline__ void flush1() {
     h0 += b0 & 0x00FF00FFu;
     h1 += (b0 >> 8) & 0x00FF00FFu;
@@ -202,39 +207,42 @@ template <bool WIDE> struct Acc<FMT_U32, WIDE> {
 
 // 10-bit lanes: a word holds samples 0..2 in bits [0,10), [10,20),
 // [20,30).  Four channels of 8-bit samples fit a lane (4 * 255 < 1024), so
-// every group of four goes straight to three 32-bit sums: u0 and u2 take
-// lanes 0 and 2, u1 takes lane 1 in place (scaled by 2^10: the plan keeps
-// nchans * 255 * 2^10 below 2^32), which saves its shift.
+// a group of four is summed lane-parallel into a.  Then:
+//   z += a                the plain 32-bit sum of every group: lanes carry
+//                         into each other, modulo 2^32
+//   w += a & 0x3FF003FF   lanes 0 and 2 apart: lane 0 in [0,20) for the
+//                         whole item (nchans * 255 < 2^20), lane 2 in
+//                         [20,32) for four groups, then moved into u2
+// and lane 1 is what z holds beyond lanes 0 and 2:
+// (z - lane0 - lane2 * 2^20) mod 2^32 = lane1 * 2^10, exact since
+// lane1 < 2^22.  The plan stages 10-bit lanes for at most 4112 channels.
 template <bool WIDE> struct Acc<FMT_TRI, WIDE> {
-  uint32_t t, u0, u1, u2;
-  __device__ __forceinline__ void zero() { t = u0 = u1 = u2 = 0u; }
+  uint32_t z, w, u2;
+  __device__ __forceinline__ void zero() { z = w = u2 = 0u; }
   __device__ __forceinline__ void add4(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
-    t = t + x0 + x1;
-    t = t + x2 + x3;
+    const uint32_t a = (x0 + x1) + (x2 + x3);
+    z += a;
+    w += a & 0x3FF003FFu;
   }
-  __device__ __forceinline__ void flush0() {
-    u0 += t & 0x3FFu;
-    u1 += t & 0xFFC00u;
-    u2 += t >> 20;
-    t = 0u;
-  }
-  // two groups of four channels, each summed in the 10-bit lanes, then
-  // widened together: one add per sum for both
-  __device__ __forceinline__ void add8_flush(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
-                                             uint32_t x4, uint32_t x5, uint32_t x6,
-                                             uint32_t x7) {
+  __device__ __forceinline__ void flush0() {}
+  // two groups of four channels (lane 2 of w then holds two such pairs)
+  __device__ __forceinline__ void add8(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
+                                       uint32_t x4, uint32_t x5, uint32_t x6, uint32_t x7) {
     const uint32_t a = (x0 + x1) + (x2 + x3);
     const uint32_t c = (x4 + x5) + (x6 + x7);
-    u0 += (a & 0x3FFu) + (c & 0x3FFu);
-    u1 += (a & 0xFFC00u) + (c & 0xFFC00u);
-    u2 += (a >> 20) + (c >> 20);
+    z = z + a + c;
+    w = w + (a & 0x3FF003FFu) + (c & 0x3FF003FFu);
   }
-  __device__ __forceinline__ void flush1() {}
+  // every four groups
+  __device__ __forceinline__ void flush1() {
+    u2 += w >> 20;
+    w &= 0xFFFFFu;
+  }
   __device__ __forceinline__ void flush2() {}
   __device__ __forceinline__ void final(uint32_t v[3]) {
-    flush0();
-    v[0] = u0;
-    v[1] = u1 >> 10;
+    flush1();
+    v[0] = w;
+    v[1] = (z - w - (u2 << 20)) >> 10;
     v[2] = u2;
   }
 };
@@ -509,6 +517,12 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       }
     };
 
+    // pairs of 4-channel groups per step (the item's chunk size allows it)
+    bool paired = false;
+    if constexpr (FMT == FMT_NIB)
+      paired = p.f0 == 1 && p.f1 >= 2 && (cc & 7) == 0 && (cc >> 3) <= (p.f1 >> 1);
+    if constexpr (FMT == FMT_TRI) paired = (cc & 7) == 0;
+
     Acc<FMT, WIDE> acc[DPW][K];
 #pragma unroll
     for (int i = 0; i < DPW; ++i)
@@ -581,29 +595,53 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       // (c) shift-and-sum over the chunk, four channels per group
       const uint32_t* const sa = s_addr + buf * n_entries;
       const uint32_t lane_off = smem_addr(landing + buf * buf_words) + (uint32_t)lane * 4u;
-      bool paired = false;
-      if constexpr (FMT == FMT_NIB)
-        paired = p.f0 == 1 && p.f1 >= 2 && (cc & 7) == 0 && (cc >> 3) <= (p.f1 >> 1);
-      if constexpr (FMT == FMT_TRI) paired = (cc & 7) == 0;
       if (warp * DPW >= nd) {
         // every trial slot of this warp is past the block's last trial: its
         // sums would be discarded (a short last block, a short sub-band
         // group), so the warp only stages
       } else if (paired) {
-        // 2-bit input: pairs of 4-channel groups widened together; a pair
-        // adds at most two group sums to a byte lane, so byte lanes take
-        // f1/2 pairs between 16-bit flushes.  The flush is taken before a
-        // chunk whose pairs would pass that, so the pair loop itself has no
-        // branch.  (8-bit input in 10-bit lanes widens every pair to 32
-        // bits: no flush between.)
-        if constexpr (FMT == FMT_NIB || FMT == FMT_TRI) {
+        // two 4-channel groups (channels cg..cg+7) into every accumulator
+        auto pair8 = [&](int cg) {
+#pragma unroll
+          for (int i = 0; i < DPW; ++i) {
+            const uint32_t* const e = sa + ((warp * DPW + i) << cc_log) + cg;
+            const uint4 a4 = *reinterpret_cast<const uint4*>(e);
+            const uint4 b4 = *reinterpret_cast<const uint4*>(e + 4);
+            const uint32_t q0 = a4.x + lane_off, q1 = a4.y + lane_off;
+            const uint32_t q2 = a4.z + lane_off, q3 = a4.w + lane_off;
+            const uint32_t q4 = b4.x + lane_off, q5 = b4.y + lane_off;
+            const uint32_t q6 = b4.z + lane_off, q7 = b4.w + lane_off;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+              if constexpr (FMT == FMT_NIB)
+                acc[i][j].add8_flush(lds32(q0 + 128u * j), lds32(q1 + 128u * j),
+                                     lds32(q2 + 128u * j), lds32(q3 + 128u * j),
+                                     lds32(q4 + 128u * j), lds32(q5 + 128u * j),
+                                     lds32(q6 + 128u * j), lds32(q7 + 128u * j));
+              if constexpr (FMT == FMT_TRI)
+                acc[i][j].add8(lds32(q0 + 128u * j), lds32(q1 + 128u * j),
+                               lds32(q2 + 128u * j), lds32(q3 + 128u * j),
+                               lds32(q4 + 128u * j), lds32(q5 + 128u * j),
+                               lds32(q6 + 128u * j), lds32(q7 + 128u * j));
+            }
+          }
+        };
+        if constexpr (FMT == FMT_NIB) {
+          // 2-bit input: pairs of 4-channel groups widened together; a pair
+          // adds at most two group sums to a byte lane, so byte lanes take
+          // f1/2 pairs between 16-bit flushes.  The flush is taken before a
+          // chunk whose pairs would pass that, so the pair loop itself has
+          // no branch.
           const int npairs = cc >> 3;
-          if (FMT == FMT_NIB && g1 + npairs > (p.f1 >> 1)) {
+          if (g1 + npairs > (p.f1 >> 1)) {
             g1 = 0;
 #pragma unroll
             for (int i = 0; i < DPW; ++i)
 #pragma unroll
-              for (int j = 0; j < K; ++j) acc[i][j].flush1();
+              for (int j = 0; j < K; ++j) {
+                acc[i][j].pair_fix();
+                acc[i][j].flush1();
+              }
             if (WIDE && ++g2 == p.f2) {
               g2 = 0;
 #pragma unroll
@@ -613,23 +651,18 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
             }
           }
           g1 += npairs;
-          for (int cg = 0; cg < cc; cg += 8) {
+          for (int cg = 0; cg < cc; cg += 8) pair8(cg);
+        }
+        if constexpr (FMT == FMT_TRI) {
+          // 8-bit input in 10-bit lanes: lane 2 of the separated sums holds
+          // two pairs, then moves to its 32-bit sum
+          for (int cg = 0; cg < cc; cg += 16) {
+            pair8(cg);
+            if (cc > 8) pair8(cg + 8);
 #pragma unroll
-            for (int i = 0; i < DPW; ++i) {
-              const uint32_t* const e = sa + ((warp * DPW + i) << cc_log) + cg;
-              const uint4 a4 = *reinterpret_cast<const uint4*>(e);
-              const uint4 b4 = *reinterpret_cast<const uint4*>(e + 4);
-              const uint32_t q0 = a4.x + lane_off, q1 = a4.y + lane_off;
-              const uint32_t q2 = a4.z + lane_off, q3 = a4.w + lane_off;
-              const uint32_t q4 = b4.x + lane_off, q5 = b4.y + lane_off;
-              const uint32_t q6 = b4.z + lane_off, q7 = b4.w + lane_off;
+            for (int i = 0; i < DPW; ++i)
 #pragma unroll
-              for (int j = 0; j < K; ++j)
-                acc[i][j].add8_flush(lds32(q0 + 128u * j), lds32(q1 + 128u * j),
-                                     lds32(q2 + 128u * j), lds32(q3 + 128u * j),
-                                     lds32(q4 + 128u * j), lds32(q5 + 128u * j),
-                                     lds32(q6 + 128u * j), lds32(q7 + 128u * j));
-            }
+              for (int j = 0; j < K; ++j) acc[i][j].flush1();
           }
         }
       } else
@@ -665,6 +698,14 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
             }
           }
         }
+      }
+    }
+    if constexpr (FMT == FMT_NIB) {
+      if (paired) {
+#pragma unroll
+        for (int i = 0; i < DPW; ++i)
+#pragma unroll
+          for (int j = 0; j < K; ++j) acc[i][j].pair_fix();
       }
     }
     // all warps are done with this item's buffers before the next prologue

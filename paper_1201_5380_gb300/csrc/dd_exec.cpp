@@ -16,7 +16,7 @@ int fmt_for_nbits(int nbits, int nchans) {
     case 1:
     case 2: return FMT_NIB;
     case 4: return FMT_BYTE;
-    case 8: return (int64_t)nchans * 255 * 1024 < ((int64_t)1 << 32) ? FMT_TRI : FMT_HALF;
+    case 8: return (int64_t)nchans * 255 < ((int64_t)1 << 20) ? FMT_TRI : FMT_HALF;
     case 32: return FMT_F32;
     default: return -1;
   }
@@ -127,7 +127,8 @@ static void flush_periods(int fmt, int vmax, int nchan_max, bool* wide, int* f0,
       *wide = (int64_t)nchan_max * vmax > 65535;
       break;
     case FMT_TRI:
-      *f0 = 1;  // every group of 4 channels goes straight to 32-bit sums
+      *f0 = 1;  // every group of 4 channels leaves the 10-bit lanes
+      *f1 = 4;  // lane 2 of the separated sums holds four groups
       break;
     case FMT_F32:
       *f0 = 8;  // 32 channels per FP32 partial sum

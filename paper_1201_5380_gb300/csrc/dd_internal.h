@@ -397,8 +397,8 @@ dd_status stage_direct_image(Plan& p, const void* in, int nbits, int64_t in_stri
 dd_status cuda_status(cudaError_t e);
 // Staged format of the direct transform for nbits input over nchans
 // channels (-1: unsupported nbits).  8-bit input takes 10-bit lanes, three
-// samples a word, while the middle lane's in-place sums fit 32 bits
-// (nchans * 255 * 2^10 < 2^32), else 16-bit lanes.
+// samples a word, while a lane's whole sum fits 20 bits (nchans * 255 <
+// 2^20, up to 4112 channels), else 16-bit lanes.
 int fmt_for_nbits(int nbits, int nchans);
 int vmax_for_nbits(int nbits);
 

@@ -282,13 +282,13 @@ def test_scaled_output_rejected_where_uint32_rows_are_required():
         dd.Stream(plan, 2, 1000)
 
 
-@pytest.mark.parametrize("nchans", [16448, 16449])
+@pytest.mark.parametrize("nchans", [4112, 4113])
 def test_8bit_lane_sums_at_the_channel_limit(orc, nchans):
-    """8-bit input is staged three samples a word in 10-bit lanes, with the
-    middle lane summed in place (scaled by 2^10) while nchans * 255 * 2^10 <
-    2^32, i.e. up to 16448 channels; one channel more stages 16-bit lanes.
-    Both sides of the limit, at the largest sums (every sample 255) and on
-    random samples, equal the oracle."""
+    """8-bit input is staged three samples a word in 10-bit lanes while a
+    lane's whole sum fits 20 bits (nchans * 255 < 2^20), i.e. up to 4112
+    channels; one channel more stages 16-bit lanes.  Both sides of the
+    limit, at the largest sums (every sample 255) and on random samples,
+    equal the oracle."""
     torch_cuda()
     plan = dd.Plan(nchans, 64e-6, 1500.0, -0.01, dms=[0.0, 40.0, 90.0])
     nsamps = 701
