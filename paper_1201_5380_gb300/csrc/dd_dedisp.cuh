@@ -503,15 +503,17 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       const uint32_t words = has ? (uint32_t)min(want, row_words - wi) : 0u;
       const uint32_t tab_bytes = (uint32_t)n_entries * 4u;
       const uint32_t total = __reduce_add_sync(0xffffffffu, words * 4u) + tab_bytes;
+      // No proxy fence here: the copies overwrite words that the block only
+      // read since they last landed (ordered by the barrier), except the
+      // zero-filled windows of channels past the band, whose writers fence
+      // before that barrier.
       if (lane == 0) {
         mbar_arrive_expect_tx(bar, total);
-        fence_proxy_async_smem();
         tma_load_1d(smem_addr(s_addr + nb * n_entries), atab + (int64_t)k * n_entries, tab_bytes,
                     bar);
       }
       __syncwarp();
       if (words) {
-        fence_proxy_async_smem();
         tma_load_1d(smem_addr(landing + nb * buf_words + lane * nwl),
                     img + (int64_t)cabs * row_words + wi, words * 4u, bar);
       }
