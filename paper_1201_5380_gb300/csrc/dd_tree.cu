@@ -234,19 +234,36 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_stage1(const TreeS1 p) {
 }
 
 struct TreeS2 {
-  const uint16_t* S;      // stage-1 rows, 16-bit samples
-  int64_t s_pitch;        // samples per S row
+  const uint32_t* S;      // stage-1 rows, two 16-bit samples per word
+  int64_t s_pitch;        // words per S row
   const int2* tab;        // [trial][sub-band] {S row, shift}
   int nsb, ndm;
+  int flush;              // sub-bands a 16-bit lane sum takes before widening
+  int vec_out;            // rows 8-byte aligned: pairs of samples stored at once
   int64_t nsamps;
   uint32_t* out;
   int64_t out_stride;
 };
 
 constexpr int kS2Warps = 8;  // trials per block
-constexpr int kS2K = 8;      // samples per lane (stride 32)
+constexpr int kS2W = 8;      // words per lane (two samples each, stride 32 words)
+constexpr int kS2Tile = 64 * kS2W;  // samples per warp
+// S words stage 2 may read past the last sample it uses (whole words of the
+// last tile, and the word after them): the allocation carries them
+constexpr int64_t kS2SlackWords = 32 * kS2W + 64;
 
-__global__ void __launch_bounds__(kS2Warps * 32) k_tree_stage2(const TreeS2 p) {
+// A warp sums one trial over a tile of 512 samples: lane l holds samples
+// 2(l + 32j) and 2(l + 32j) + 1 of the tile (j < 8) in one word, two 16-bit
+// lanes.  A sub-band's shifted row is read a word per lane and sample pair;
+// an odd shift takes the word after each lane's from the next lane (a warp
+// shuffle; lane 31 from lane 0's next word) and funnel-shifts the pair into
+// place, so every load is an aligned, coalesced 32-bit load.  The next
+// sub-band's words are loaded while this one's are summed (the kernel is
+// bound by the loads in flight).  WIDEN: the 16-bit sums are widened into
+// 32-bit sums every p.flush sub-bands (the host's bound: flush * N' * max
+// sample < 2^16); otherwise only at the end.
+template <bool WIDEN>
+__global__ void __launch_bounds__(kS2Warps * 32, 5) k_tree_stage2(const TreeS2 p) {
   extern __shared__ int2 s_tab[];
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -254,31 +271,101 @@ __global__ void __launch_bounds__(kS2Warps * 32) k_tree_stage2(const TreeS2 p) {
   // blocks running together read the same stage-1 tiles, from L2
   const int ntb = (p.ndm + kS2Warps - 1) / kS2Warps;
   const int d0 = (int)(blockIdx.x % ntb) * kS2Warps;
-  const int64_t t0 = (int64_t)(blockIdx.x / ntb) * (32 * kS2K);
+  const int64_t t0 = (int64_t)(blockIdx.x / ntb) * kS2Tile;
   const int nd = min(kS2Warps, p.ndm - d0);
   for (int e = threadIdx.x; e < nd * p.nsb; e += blockDim.x)
     s_tab[e] = p.tab[(int64_t)d0 * p.nsb + e];
   __syncthreads();
   if (warp >= nd) return;
   const int d = d0 + warp;
-  uint32_t acc[kS2K];
-#pragma unroll
-  for (int j = 0; j < kS2K; ++j) acc[j] = 0u;
   const int2* tab = s_tab + warp * p.nsb;
-  // samples past the gulp are neither read nor written (their reads could
-  // pass the end of the last stage-1 row)
-  const int64_t left = p.nsamps - t0 - lane;
-  for (int n = 0; n < p.nsb; ++n) {
+  uint32_t h[kS2W], u[WIDEN ? 2 * kS2W : 1];
+#pragma unroll
+  for (int j = 0; j < kS2W; ++j) h[j] = 0u;
+#pragma unroll
+  for (int j = 0; j < (WIDEN ? 2 * kS2W : 1); ++j) u[j] = 0u;
+
+  // words of sub-band n (and lane 0's word after them); returns the shift's
+  // parity
+  auto fetch = [&](int n, uint32_t (&w)[kS2W], uint32_t& tail) -> bool {
     const int2 rs = tab[n];
-    const uint16_t* row = p.S + (int64_t)rs.x * p.s_pitch + rs.y + t0 + lane;
+    const int64_t e0 = t0 + rs.y;  // sample of the row under the tile's first output
+    const uint32_t* src = p.S + (int64_t)rs.x * p.s_pitch + (e0 >> 1) + lane;
 #pragma unroll
-    for (int j = 0; j < kS2K; ++j)
-      if (32 * j < left) acc[j] += __ldg(row + 32 * j);
+    for (int j = 0; j < kS2W; ++j) w[j] = __ldg(src + 32 * j);
+    tail = lane == 0 ? __ldg(src + 32 * kS2W) : 0u;
+    return (e0 & 1) != 0;
+  };
+  auto accumulate = [&](const uint32_t (&w)[kS2W], uint32_t tail, bool odd) {
+    if (odd) {
+#pragma unroll
+      for (int j = 0; j < kS2W; ++j) {
+        // lanes 1..31 send their word j, lane 0 its next one (for lane 31)
+        const uint32_t give = lane == 0 ? (j + 1 < kS2W ? w[(j + 1) % kS2W] : tail) : w[j];
+        const uint32_t nx = __shfl_sync(0xffffffffu, give, (lane + 1) & 31);
+        h[j] += __funnelshift_r(w[j], nx, 16);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kS2W; ++j) h[j] += w[j];
+    }
+  };
+  auto widen = [&]() {
+    if constexpr (WIDEN) {
+#pragma unroll
+      for (int j = 0; j < kS2W; ++j) {
+        u[2 * j] += h[j] & 0xFFFFu;
+        u[2 * j + 1] += h[j] >> 16;
+        h[j] = 0u;
+      }
+    }
+  };
+
+  uint32_t wa[kS2W], wb[kS2W], ta, tb;
+  bool oa = fetch(0, wa, ta);
+  int g = 0;
+  for (int n = 0; n < p.nsb; n += 2) {
+    // sub-bands n (in wa) and n + 1 (in wb); the loads of the next one are
+    // in flight while each is summed
+    const bool two = n + 1 < p.nsb;
+    bool ob = false;
+    if (two) ob = fetch(n + 1, wb, tb);
+    accumulate(wa, ta, oa);
+    if (WIDEN && ++g == p.flush) {
+      g = 0;
+      widen();
+    }
+    if (!two) break;
+    if (n + 2 < p.nsb) oa = fetch(n + 2, wa, ta);
+    accumulate(wb, tb, ob);
+    if (WIDEN && ++g == p.flush) {
+      g = 0;
+      widen();
+    }
   }
-  uint32_t* o = p.out + (int64_t)d * p.out_stride + t0 + lane;
+  uint32_t v[2 * kS2W];
+  if constexpr (WIDEN) {
+    widen();
 #pragma unroll
-  for (int j = 0; j < kS2K; ++j)
-    if (t0 + lane + 32 * j < p.nsamps) o[32 * j] = acc[j];
+    for (int j = 0; j < 2 * kS2W; ++j) v[j] = u[WIDEN ? j : 0];
+  } else {
+#pragma unroll
+    for (int j = 0; j < kS2W; ++j) {
+      v[2 * j] = h[j] & 0xFFFFu;
+      v[2 * j + 1] = h[j] >> 16;
+    }
+  }
+  uint32_t* o = p.out + (int64_t)d * p.out_stride;
+#pragma unroll
+  for (int j = 0; j < kS2W; ++j) {
+    const int64_t t = t0 + 2 * (lane + 32 * j);
+    if (p.vec_out && t + 2 <= p.nsamps) {
+      *reinterpret_cast<uint2*>(o + t) = make_uint2(v[2 * j], v[2 * j + 1]);
+    } else {
+      if (t < p.nsamps) o[t] = v[2 * j];
+      if (t + 1 < p.nsamps) o[t + 1] = v[2 * j + 1];
+    }
+  }
 }
 
 template <int NSUB>
@@ -374,7 +461,8 @@ dd_status exec_tree(Plan& p, const ExecArgs& a) {
   // S rows: every stage-1 tile writes T samples; stage 2 reads up to len1
   const int64_t pitch = ((tiles * T + 63) / 64) * 64;    // samples
   const int rows = p.tree_roff[nsb];
-  if ((e = p.d_tree_S.ensure((size_t)rows * pitch * 2)) != cudaSuccess) return cuda_status(e);
+  if ((e = p.d_tree_S.ensure(((size_t)rows * pitch / 2 + kS2SlackWords) * 4)) != cudaSuccess)
+    return cuda_status(e);
   TreeS1 s1;
   s1.in = static_cast<const uint8_t*>(a.in);
   s1.in_stride = a.in_row_stride;
@@ -390,19 +478,25 @@ dd_status exec_tree(Plan& p, const ExecArgs& a) {
     if ((e = stage1(Np, s1, tiles, nsb, a.st)) != cudaSuccess) return cuda_status(e);
   }
   TreeS2 s2;
-  s2.S = static_cast<const uint16_t*>(p.d_tree_S.p);
-  s2.s_pitch = pitch;
+  s2.S = static_cast<const uint32_t*>(p.d_tree_S.p);
+  s2.s_pitch = pitch / 2;
   s2.tab = static_cast<const int2*>(p.d_tree_tab.p);
   s2.nsb = nsb;
   s2.ndm = n;
+  // a stage-1 sample is at most N' * (2^nbits - 1) (<= 128 * 255 < 2^16)
+  s2.flush = (int)(65535 / ((int64_t)Np * ((1 << a.in_nbits) - 1)));
+  s2.vec_out = (reinterpret_cast<uintptr_t>(a.out) & 7) == 0 && (a.out_stride & 1) == 0;
   s2.nsamps = a.nsamps_out;
   s2.out = static_cast<uint32_t*>(a.out);
   s2.out_stride = a.out_stride;
-  const int64_t t2 = (a.nsamps_out + 32 * kS2K - 1) / (32 * kS2K);
+  const int64_t t2 = (a.nsamps_out + kS2Tile - 1) / kS2Tile;
   const unsigned grid = (unsigned)(t2 * ((n + kS2Warps - 1) / kS2Warps));
   const size_t smem = (size_t)kS2Warps * nsb * sizeof(int2);
   KernelTimer kt(&p, DD_KERNEL_STAGE2, a.st);
-  k_tree_stage2<<<grid, kS2Warps * 32, smem, a.st>>>(s2);
+  if (s2.flush < nsb)
+    k_tree_stage2<true><<<grid, kS2Warps * 32, smem, a.st>>>(s2);
+  else
+    k_tree_stage2<false><<<grid, kS2Warps * 32, smem, a.st>>>(s2);
   return cuda_status(cudaGetLastError());
 }
 
