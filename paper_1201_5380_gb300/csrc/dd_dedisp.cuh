@@ -483,48 +483,39 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       const int ca = (k << cc_log) + c;
       return ca < nchan ? __ldg(&crec[ca]) : make_int2(0, 32 * K);
     };
-    // TMA of chunk k into buffer nb.  Warp 0 (lane = channel of the chunk)
-    // sets the bytes the buffer's barrier expects and copies the offsets;
-    // the first builder thread of each channel copies that channel's window,
-    // so the copies are issued from every warp rather than all from one.  A
-    // copy may land before the expected bytes are set: the barrier's phase
-    // cannot complete before warp 0's arrival.  A window running past the
-    // end of its row (a launch over images of different lengths) is
-    // shortened: those words are beyond every valid output of this image.
-    auto window_words = [&](int k, int c, int2 r, int64_t& wi) -> uint32_t {
-      wi = t0w + r.x;
-      if (c >= cc || (k << cc_log) + c >= nchan) return 0u;
-      if (wi < 0 || wi + 4 > row_words) wi = 0;  // redirected; the copier flags it
+    // TMA of chunk k (warp 0): the offsets, then each channel's window.  A
+    // window running past the end of its row (a launch over images of
+    // different lengths) is shortened: those words are beyond every valid
+    // output of this image.
+    auto issue = [&](int k, int nb, int2 r) {
+      const uint32_t bar = bar0 + 8u * nb;
+      const int c0 = k << cc_log;
+      const int cabs = min(c0 + lane, nchan - 1);
+      int64_t wi = t0w + r.x;
+      const bool has = lane < cc && c0 + lane < nchan;
+      if (has && (wi < 0 || wi + 4 > row_words)) {
+        atomicOr(p.status, DEV_BAD_READ);
+        wi = 0;
+      }
       // the words this channel's trials read (plus the next word, which the
       // lane-shift build reads), not the block's whole window
       const int64_t want = min((int64_t)nwl, (int64_t)((r.y + 4 + 3) & ~3));
-      return (uint32_t)min(want, row_words - wi);
-    };
-    // No proxy fence on the issuing side: the copies overwrite words that the
-    // block only read since they last landed (ordered by the barrier), except
-    // the zero-filled windows of channels past the band, whose writers fence
-    // before that barrier.
-    auto expect = [&](int k, int nb, int2 r) {
-      int64_t wi;
-      const uint32_t words = window_words(k, lane, r, wi);
+      const uint32_t words = has ? (uint32_t)min(want, row_words - wi) : 0u;
       const uint32_t tab_bytes = (uint32_t)n_entries * 4u;
       const uint32_t total = __reduce_add_sync(0xffffffffu, words * 4u) + tab_bytes;
+      // No proxy fence here: the copies overwrite words that the block only
+      // read since they last landed (ordered by the barrier), except the
+      // zero-filled windows of channels past the band, whose writers fence
+      // before that barrier.
       if (lane == 0) {
-        mbar_arrive_expect_tx(bar0 + 8u * nb, total);
+        mbar_arrive_expect_tx(bar, total);
         tma_load_1d(smem_addr(s_addr + nb * n_entries), atab + (int64_t)k * n_entries, tab_bytes,
-                    bar0 + 8u * nb);
+                    bar);
       }
-    };
-    const bool leader = (tid & ((1 << tpc_log) - 1)) == 0;
-    auto copy_own = [&](int k, int nb, int2 r) {
-      int64_t wi;
-      const uint32_t words = window_words(k, bc, r, wi);
+      __syncwarp();
       if (words) {
-        const int64_t w0 = t0w + r.x;
-        if (w0 < 0 || w0 + 4 > row_words) atomicOr(p.status, DEV_BAD_READ);
-        tma_load_1d(smem_addr(landing + nb * buf_words + bc * nwl),
-                    img + (int64_t)((k << cc_log) + bc) * row_words + wi, words * 4u,
-                    bar0 + 8u * nb);
+        tma_load_1d(smem_addr(landing + nb * buf_words + lane * nwl),
+                    img + (int64_t)cabs * row_words + wi, words * 4u, bar);
       }
     };
 
@@ -543,18 +534,17 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
 
     // prologue: chunk 0
     int2 rec_w = make_int2(0, 0);  // warp 0: window record of the next chunk to issue
-    int2 rec_b = rec_of(0, bc);    // builders: record of their channel's window
-    if (warp == 0) expect(0, kk & 1, rec_of(0, lane));
-    if (leader) copy_own(0, kk & 1, rec_b);
-    int span = rec_b.y;  // builders: words of this chunk's window
+    if (warp == 0) issue(0, kk & 1, rec_of(0, lane));
+    int span = COPIES ? rec_of(0, bc).y : 0;  // builders: words of this chunk's window
 
     for (int k = 0; k < nchunks; ++k, ++kk) {
       const int buf = kk & 1;
       const int c0 = k << cc_log;
       const bool more = k + 1 < nchunks;
+      int span_next = 0;
       if (more) {
         if (warp == 0) rec_w = rec_of(k + 1, lane);
-        rec_b = rec_of(k + 1, bc);
+        if (COPIES) span_next = rec_of(k + 1, bc).y;
       }
       // (a) wait for the chunk's windows and offsets, then build the SPW
       //     shifted copies as far as the chunk's trials read
@@ -602,11 +592,8 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) k_dedisp(con
       }
       __syncthreads();
       // (b) next chunk's TMA (its buffers were released by the barrier above)
-      if (more) {
-        if (warp == 0) expect(k + 1, buf ^ 1, rec_w);
-        if (leader) copy_own(k + 1, buf ^ 1, rec_b);
-      }
-      span = rec_b.y;
+      if (more && warp == 0) issue(k + 1, buf ^ 1, rec_w);
+      span = span_next;
       // (c) shift-and-sum over the chunk, four channels per group
       const uint32_t* const sa = s_addr + buf * n_entries;
       const uint32_t lane_off = smem_addr(landing + buf * buf_words) + (uint32_t)lane * 4u;
