@@ -334,6 +334,22 @@ bool out_vec_ok(const void* out, int64_t stride_elems, int esz) {
   return !(reinterpret_cast<uintptr_t>(out) & 15) && !((stride_elems * esz) & 15);
 }
 
+// Time tiles per work item.  An item of one or two chunks (the 32 channels of
+// a sub-band stage) spends most of its time starting: the item counter, the
+// block bounds, geometry and window records, then the first chunk's copy,
+// one dependent latency after another.  Such items cover up to four
+// consecutive tiles of their trial block, staged as one stream of chunks, so
+// that start is paid once per group of tiles; the grid keeps at least eight
+// items per SM.
+static int tiles_per_item_for(const Plan& p, int nchan, int cc_cap, int64_t tiles,
+                              int64_t items_per_tile) {
+  const int chunks = (nchan + cc_cap - 1) / cc_cap;
+  int r = chunks <= 1 ? 4 : (chunks == 2 ? 2 : 1);
+  const int64_t want = 8 * (int64_t)std::max(1, p.num_sms);
+  while (r > 1 && ((tiles + r - 1) / r) * items_per_tile < want) r >>= 1;
+  return r;
+}
+
 // Fill launch parameters for a set of segments sharing one staged format.
 // tune: the launch's tiling (words per lane resolved, see tuning_for).
 static dd_status finish_launch(Plan& p, const Tuning& tune, int fmt, int outk, int vmax,
@@ -349,11 +365,20 @@ static dd_status finish_launch(Plan& p, const Tuning& tune, int fmt, int outk, i
   int cc_cap = 4;
   while (cc_cap * 2 <= tune.chans_per_chunk) cc_cap *= 2;
 
+  bool wide;
+  int f0, f1, f2;
+  flush_periods(fmt, vmax, nchan_max, &wide, &f0, &f1, &f2);
+  // items of several time tiles where the multi-tile kernel is compiled for
+  // the launch's kernel (scaled output runs the OUT_NARROW kernel)
+  const int outk_run = outk == OUT_U32 && p.out_bits < 32 ? OUT_NARROW : outk;
+  const bool mt_ok = multi_tile_compiled(fmt, outk_run, wide, cfg);
+
   L->fmt = fmt;
   L->outk = outk;
   L->cfg = cfg;
   L->segs.clear();
   int64_t items = 0;
+  bool multi = false;
   for (auto& s : specs) {
     Seg g = s.seg;
     if (g.n_groups < 1) g.n_groups = 1;
@@ -361,14 +386,16 @@ static dd_status finish_launch(Plan& p, const Tuning& tune, int fmt, int outk, i
     if (g.ndm <= 0 || g.nsamps <= 0) continue;
     if (!g.blk) g.n_dmblk = (g.ndm + B - 1) / B;
     const int64_t tiles = (g.nsamps + T - 1) / T;
+    g.tile0 = 0;
+    g.tile_end = tiles;
+    g.tiles_per_item =
+        mt_ok ? tiles_per_item_for(p, g.nchan, cc_cap, tiles, (int64_t)g.n_dmblk * g.n_groups) : 1;
+    multi = multi || g.tiles_per_item > 1;
     g.item_begin = items;
-    items += (int64_t)g.n_dmblk * g.n_groups * tiles;
+    items += (int64_t)g.n_dmblk * g.n_groups * ((tiles + g.tiles_per_item - 1) / g.tiles_per_item);
     L->segs.push_back(g);
   }
   if (L->segs.size() > (size_t)kMaxSegs) return DD_ERR_INVALID_ARG;
-  bool wide;
-  int f0, f1, f2;
-  flush_periods(fmt, vmax, nchan_max, &wide, &f0, &f1, &f2);
   if (outk == OUT_HALFIMG && (wide || (int64_t)nchan_max * std::max(vmax, 1) > 65535))
     return DD_ERR_OVERFLOW;
   L->wide = wide;
@@ -380,6 +407,7 @@ static dd_status finish_launch(Plan& p, const Tuning& tune, int fmt, int outk, i
   lp.f1 = f1;
   lp.f2 = f2;
   lp.n_items = items;
+  lp.multi_tile = multi ? 1 : 0;
   lp.vec_out = vec_out ? 1 : 0;
   // scaled low-bit output (Sec. 4.3): keep the top out_bits of the range a
   // sum can reach, nchan * vmax
@@ -433,7 +461,7 @@ static dd_status finish_launch(Plan& p, const Tuning& tune, int fmt, int outk, i
   lp.nww = uniform ? unww : 0;
   int per_sm = 0;
   cudaError_t e = dedisp_max_blocks_per_sm(fmt, L->outk, wide, cfg, lp.per_block_geo != 0,
-                                           L->smem, &per_sm);
+                                           lp.multi_tile != 0, L->smem, &per_sm);
   if (e != cudaSuccess) return cuda_status(e);
   if (per_sm < 1) return DD_ERR_INVALID_ARG;
   const int64_t resident = (int64_t)per_sm * std::max(1, p.num_sms);
@@ -673,8 +701,10 @@ static dd_status exec_direct_host_out(Plan& p, const ExecArgs& a, int fmt, const
       w_done = w_need;
     }
     LaunchPlan Lq = L;
+    const int rq = Lq.lp.segs[0].tiles_per_item;
     Lq.lp.segs[0].tile0 = t0;
-    Lq.lp.n_items = (t1 - t0) * per_tile;
+    Lq.lp.segs[0].tile_end = t1;
+    Lq.lp.n_items = ((t1 - t0 + rq - 1) / rq) * per_tile;
     Lq.grid = (int)std::min<int64_t>(L.grid, Lq.lp.n_items);
     if ((s = run_launch(p, Lq, a.st)) != DD_OK) return s;
     // output samples [t0 T, t1 T) of every trial are final: copy them out

@@ -60,7 +60,9 @@ enum : uint32_t {
 // the last group) x nsamps outputs over one image.  Group g uses the image,
 // delay table and output advanced by g times the group strides (sub-bands in
 // sub-band stage 1, trial groups in stage 2; a direct job has one group).
-// Items of a segment are (time tile, group, trial block), trial block fastest.
+// Items of a segment are (tile group, group, trial block), trial block
+// fastest; a tile group is tiles_per_item consecutive time tiles, which one
+// item stages and sums as one stream of chunks.
 struct Seg {
   const int32_t* blk;     // optional trial-block starts (n_dmblk + 1 entries,
                           // device); null = regular blocks of B trials
@@ -71,8 +73,8 @@ struct Seg {
   int64_t out_stride;     // output row pitch (elements, or words for OUT_HALFIMG)
   int64_t nsamps;         // outputs per trial
   int64_t item_begin;     // first global item index of this segment
-  int64_t tile0;          // time tile of the segment's first item (items cover
-                          // tiles tile0 .. tile0 + n_items / per-tile items)
+  int64_t tile0;          // first time tile of the segment's first item
+  int64_t tile_end;       // the segment's items cover tiles [tile0, tile_end)
   int64_t g_img;          // per-group image offset, words
   int64_t g_out;          // per-group output offset, elements (words)
   int32_t g_delay;        // per-group delay-table offset, elements
@@ -82,6 +84,7 @@ struct Seg {
   int32_t n_dmblk;        // ceil(ndm / trials per block)
   int32_t delay_stride;   // elements between trial rows of the delay table
   int32_t nchan;          // channels summed
+  int32_t tiles_per_item; // time tiles per item (>= 1)
   int32_t lo_slack;       // max_{block,c} delay(d0,c) - min_{d in block} delay(d,c)
   // Staging tables of the launch geometry (built on the host, see StageTab):
   const uint32_t* atab;   // [group][block: atab_blk][chunk][trial slot][channel
@@ -116,7 +119,7 @@ struct LaunchParams {
   int32_t vec_out;   // 1 if every output row/tile start is 16-byte aligned
   int32_t out_bits;  // 32, or 16 / 8: scaled output (OUT_U32 launches)
   int32_t out_shift; // scaled output = min(sum >> out_shift, 2^out_bits - 1)
-  int32_t pad_;
+  int32_t multi_tile; // 1 if any segment's items cover several tiles (MT kernel)
 };
 
 // The plan's status buffer: the status word, then kItemCounters launch
@@ -142,8 +145,11 @@ constexpr int kNumTileCfgs = 6;
 // Host launchers (dd_kernels_*.cu).
 cudaError_t launch_dedisp(int fmt, int outk, bool wide, int cfg, const LaunchParams& p,
                           int grid, size_t smem, cudaStream_t st);
-cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, bool pbg, size_t smem,
-                                     int* nblk);
+cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, bool pbg, bool mt,
+                                     size_t smem, int* nblk);
+// Whether the multi-tile kernel (items of several time tiles) is compiled
+// for this staged format, output kind, accumulator width and tile shape.
+bool multi_tile_compiled(int fmt, int outk, bool wide, int cfg);
 // Image words [w_first, words) of every channel row, in staged format fmt
 // (fmt_for_nbits, or FMT_HALF for 8-bit input of the sub-band method).
 cudaError_t launch_corner_turn(int nbits, int fmt, const uint8_t* in, int64_t in_stride,

@@ -17,10 +17,25 @@ cudaError_t dispatch_word(int, int, bool, int, bool, const LaunchParams*, int, s
                           cudaStream_t, int*);
 cudaError_t dispatch_tri(int, bool, int, bool, const LaunchParams*, int, size_t, cudaStream_t,
                          int*);
+cudaError_t dispatch_nib_mt(int, bool, int, bool, const LaunchParams*, int, size_t, cudaStream_t,
+                            int*);
+cudaError_t dispatch_half_mt(int, bool, int, bool, const LaunchParams*, int, size_t,
+                             cudaStream_t, int*);
 
-static cudaError_t dispatch(int fmt, int outk, bool wide, int cfg, bool pbg,
+bool multi_tile_compiled(int fmt, int outk, bool wide, int cfg) {
+  if (fmt == FMT_NIB) return outk == OUT_HALFIMG && !wide && cfg == 0;
+  if (fmt == FMT_HALF) return cfg == 5 && ((outk == OUT_HALFIMG && !wide) || outk == OUT_U32);
+  return false;
+}
+
+static cudaError_t dispatch(int fmt, int outk, bool wide, int cfg, bool pbg, bool mt,
                             const LaunchParams* p, int grid, size_t smem, cudaStream_t st,
                             int* occ) {
+  if (mt) {
+    if (fmt == FMT_NIB) return dispatch_nib_mt(outk, wide, cfg, pbg, p, grid, smem, st, occ);
+    if (fmt == FMT_HALF) return dispatch_half_mt(outk, wide, cfg, pbg, p, grid, smem, st, occ);
+    return cudaErrorInvalidValue;
+  }
   switch (fmt) {
     case FMT_NIB: return dispatch_nib(outk, wide, cfg, pbg, p, grid, smem, st, occ);
     case FMT_BYTE: return dispatch_byte(outk, wide, cfg, pbg, p, grid, smem, st, occ);
@@ -32,13 +47,14 @@ static cudaError_t dispatch(int fmt, int outk, bool wide, int cfg, bool pbg,
 
 cudaError_t launch_dedisp(int fmt, int outk, bool wide, int cfg, const LaunchParams& p,
                           int grid, size_t smem, cudaStream_t st) {
-  return dispatch(fmt, outk, wide, cfg, p.per_block_geo != 0, &p, grid, smem, st, nullptr);
+  return dispatch(fmt, outk, wide, cfg, p.per_block_geo != 0, p.multi_tile != 0, &p, grid, smem,
+                  st, nullptr);
 }
 
-cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, bool pbg, size_t smem,
-                                     int* nblk) {
+cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, bool pbg, bool mt,
+                                     size_t smem, int* nblk) {
   *nblk = 0;
-  return dispatch(fmt, outk, wide, cfg, pbg, nullptr, 0, smem, nullptr, nblk);
+  return dispatch(fmt, outk, wide, cfg, pbg, mt, nullptr, 0, smem, nullptr, nblk);
 }
 
 // Two mbarriers, then two buffers each of the landing windows (cc x

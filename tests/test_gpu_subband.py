@@ -103,3 +103,24 @@ def test_subband_full_size_nominal_trials_exact(orc):
     ts = rng.integers(0, G, 2000)
     got = out[torch.from_numpy(ds).cuda(), torch.from_numpy(ts).cuda()].cpu().numpy()
     assert np.array_equal(got.view(np.uint32), orc.direct_points(x, 2, 1024, eff, ds, ts))
+
+
+@pytest.mark.parametrize("nbits", [2, 8])
+def test_subband_multi_tile_items_full_rows(orc, nbits):
+    """Every trial of the 1196-trial list, full rows, at 2^17 + 1237 samples.
+    The stages' work items are one or two chunks of 32 channels, so the
+    library gives each item several consecutive time tiles while at least
+    eight items per SM remain: stage 2 has 130 tiles of 1024 samples x 38
+    groups here, i.e. items of four tiles (the last of two), and stage 1
+    likewise.  Tile groups, their ragged end and the chunk stream across
+    tile boundaries are all compared with the oracle, element by element."""
+    c = configs.SUBBAND
+    plan = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0),
+                   subband=(32, 32))
+    assert plan.dm_count == 1196
+    nsamps = 131072 + 1237
+    rows = nsamps + plan.subband_max_delay
+    x = synth.uniform_packed(31 + nbits, nbits, rows, 1024, nbits)
+    got, _ = run_direct(plan, x, nbits, nsamps, subband=True)
+    ref = orc.subband(x, nbits, 1024, 32, 32, odelays(orc, plan), nsamps)
+    assert np.array_equal(got, ref), np.argwhere(got != ref)[:5]
