@@ -111,8 +111,8 @@ def test_subband_multi_tile_items_full_rows(orc, nbits):
     The stages' work items are one or two chunks of 32 channels, so the
     library gives each item several consecutive time tiles while at least
     eight items per SM remain: stage 2 has 130 tiles of 1024 samples x 38
-    groups here, i.e. items of four tiles (the last of two), and stage 1
-    likewise.  Tile groups, their ragged end and the chunk stream across
+    groups here, i.e. items of four tiles (the last of two) on 152 SMs, and
+    stage 1 likewise.  Tile groups, their ragged end and the chunk stream across
     tile boundaries are all compared with the oracle, element by element."""
     c = configs.SUBBAND
     plan = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0),
