@@ -185,22 +185,30 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_stage1(const TreeS1 p) {
     const bool words = (sub_bits % 32) == 0 &&
                        ((reinterpret_cast<uintptr_t>(p.in) | (uintptr_t)p.in_stride |
                          (uintptr_t)(bit0 >> 3)) & 3) == 0;
-    for (int q = tid; q < WW; q += kTreeThreads) {
-      const int64_t t = t0 + 2 * q;
-      const uint8_t* r0 = p.in + t * p.in_stride + (bit0 >> 3);
-      const uint8_t* r1 = r0 + p.in_stride;
-      const bool ok0 = t < p.in_rows, ok1 = t + 1 < p.in_rows;
-      if (words) {
-        for (int w = 0; w < sub_bits / 32; ++w) {
-          const uint32_t x0 = ok0 ? __ldg(reinterpret_cast<const uint32_t*>(r0) + w) : 0u;
-          const uint32_t x1 = ok1 ? __ldg(reinterpret_cast<const uint32_t*>(r1) + w) : 0u;
-          for (int j = 0; j < 32 / nb; ++j) {
-            const int c = w * (32 / nb) + j;
-            buf0[c * PW + q] = ((x0 >> (j * nb)) & vmask) | (((x1 >> (j * nb)) & vmask) << 16);
-          }
+    if (words) {
+      // one (word of the tile, 32-bit piece of the sub-band's bits) per
+      // thread, so that every thread has a share
+      const int nw = sub_bits / 32;
+      for (int e = tid; e < WW * nw; e += kTreeThreads) {
+        const int q = e / nw, w = e - q * nw;
+        const int64_t t = t0 + 2 * q;
+        const uint8_t* r0 = p.in + t * p.in_stride + (bit0 >> 3);
+        const uint8_t* r1 = r0 + p.in_stride;
+        const uint32_t x0 = t < p.in_rows ? __ldg(reinterpret_cast<const uint32_t*>(r0) + w) : 0u;
+        const uint32_t x1 =
+            t + 1 < p.in_rows ? __ldg(reinterpret_cast<const uint32_t*>(r1) + w) : 0u;
+        for (int j = 0; j < 32 / nb; ++j) {
+          const int c = w * (32 / nb) + j;
+          buf0[c * PW + q] = ((x0 >> (j * nb)) & vmask) | (((x1 >> (j * nb)) & vmask) << 16);
         }
-      } else {
-        const int sh = (int)(bit0 & 7);
+      }
+    } else {
+      const int sh = (int)(bit0 & 7);
+      for (int q = tid; q < WW; q += kTreeThreads) {
+        const int64_t t = t0 + 2 * q;
+        const uint8_t* r0 = p.in + t * p.in_stride + (bit0 >> 3);
+        const uint8_t* r1 = r0 + p.in_stride;
+        const bool ok0 = t < p.in_rows, ok1 = t + 1 < p.in_rows;
         for (int c = 0; c < NSUB; ++c) {
           const int b = sh + c * nb;
           const uint32_t x0 = ok0 ? ((uint32_t)__ldg(r0 + (b >> 3)) >> (b & 7)) & vmask : 0u;
