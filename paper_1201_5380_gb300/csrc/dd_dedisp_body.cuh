@@ -29,13 +29,17 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) DD_KERNEL(co
 
   // Chunk geometry and the staging layout it implies: the launch's, set up
   // once here, or (PBG) each trial block's, set up per work item.
+  // FINE: the chunk size is any multiple of 4 (8-bit input, three samples a
+  // word); otherwise a power of two
+  constexpr bool FINE = FMT == FMT_TRI;
   struct Geo {
     int cc, cc_log, nww, nwl, buf_words, n_entries, tpc_log, bc;
+    int tpc = 0, bq = 0;  // FINE: builder threads per channel, this thread's index among them
     uint32_t* s_addr;
   };
   auto make_geo = [&](int cc, int nww) {
     Geo g;
-    g.cc = cc;  // power of two, 4..32
+    g.cc = cc;  // power of two (FINE: multiple of 4), 4..32
     g.cc_log = 31 - __clz(cc);
     g.nww = nww;  // window words (multiple of 4)
     g.nwl = nww + 4;
@@ -47,6 +51,13 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) DD_KERNEL(co
     // the builder threads of a channel: NT / cc of them
     g.tpc_log = (31 - __clz(NT)) - g.cc_log;
     g.bc = tid >> g.tpc_log;
+    if constexpr (FINE) {
+      // (the NT mod cc threads past the last channel build nothing)
+      g.n_entries = B * cc;
+      g.tpc = NT / cc;
+      g.bc = tid / g.tpc;
+      g.bq = tid - g.bc * g.tpc;
+    }
     return g;
   };
   const Geo geo_launch = make_geo(PBG ? 4 : p.cc, PBG ? 0 : p.nww);
@@ -129,7 +140,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) DD_KERNEL(co
     uint32_t* const s_addr = G.s_addr;
     const int buf_words = G.buf_words;
     const int n_entries = G.n_entries, tpc_log = G.tpc_log, bc = G.bc;
-    const int nchunks = (nchan + cc - 1) >> cc_log;
+    const int nchunks = FINE ? (nchan + cc - 1) / cc : (nchan + cc - 1) >> cc_log;
     const uint32_t* __restrict__ atab =
         S.atab + (int64_t)grp * S.g_atab + (int64_t)blk * S.atab_blk;
 #if !DD_MT
@@ -138,7 +149,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) DD_KERNEL(co
 
     // window record of channel c0 + (warp 0: lane; builders: bc) of chunk k
     auto rec_of = [&](int k, int c) -> int2 {
-      const int ca = (k << cc_log) + c;
+      const int ca = (FINE ? k * cc : k << cc_log) + c;
       return ca < nchan ? __ldg(&crec[ca]) : make_int2(0, 32 * K);
     };
     // TMA of chunk k (warp 0): the offsets, then each channel's window.  A
@@ -152,7 +163,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) DD_KERNEL(co
     auto issue = [&](int k, int nb, int2 r) {
 #endif
       const uint32_t bar = bar0 + 8u * nb;
-      const int c0 = k << cc_log;
+      const int c0 = FINE ? k * cc : k << cc_log;
       const int cabs = min(c0 + lane, nchan - 1);
       int64_t wi = t0w + r.x;
       const bool has = lane < cc && c0 + lane < nchan;
@@ -186,7 +197,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) DD_KERNEL(co
     bool paired = false;
     if constexpr (FMT == FMT_NIB)
       paired = p.f0 == 1 && p.f1 >= 2 && (cc & 7) == 0 && (cc >> 3) <= (p.f1 >> 1);
-    if constexpr (FMT == FMT_TRI) paired = (cc & 7) == 0;
+    if constexpr (FMT == FMT_TRI) paired = true;
 
     Acc<FMT, WIDE> acc[DPW][K];
 #pragma unroll
@@ -212,7 +223,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) DD_KERNEL(co
 #endif
     for (int k = 0; k < nchunks; ++k, ++kk) {
       const int buf = kk & 1;
-      const int c0 = k << cc_log;
+      const int c0 = FINE ? k * cc : k << cc_log;
 #if DD_MT
       const bool tile_done = k + 1 == nchunks;
       const bool more = !tile_done || !last_tile;
@@ -248,9 +259,11 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) DD_KERNEL(co
         uint32_t* const land = landing + buf * buf_words;
         uint32_t* const cp = land + cc * nwl;
         const int c = bc;
-        const int nq = (min(span, nww) + 3) >> 2;
+        const int nq = (!FINE || c < cc) ? (min(span, nww) + 3) >> 2 : 0;
         const bool live = c0 + c < nchan;
-        for (int q = tid & ((1 << tpc_log) - 1); q < nq; q += (1 << tpc_log)) {
+        const int q0 = FINE ? G.bq : tid & ((1 << tpc_log) - 1);
+        const int qs = FINE ? G.tpc : 1 << tpc_log;
+        for (int q = q0; q < nq; q += qs) {
           uint4 w = make_uint4(0u, 0u, 0u, 0u);
           uint32_t w4 = 0u;
           if (live) {
@@ -294,7 +307,8 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) DD_KERNEL(co
         auto pair8 = [&](int cg) {
 #pragma unroll
           for (int i = 0; i < DPW; ++i) {
-            const uint32_t* const e = sa + ((warp * DPW + i) << cc_log) + cg;
+            const uint32_t* const e =
+                sa + (FINE ? (warp * DPW + i) * cc : (warp * DPW + i) << cc_log) + cg;
             const uint4 a4 = *reinterpret_cast<const uint4*>(e);
             const uint4 b4 = *reinterpret_cast<const uint4*>(e + 4);
             const uint32_t q0 = a4.x + lane_off, q1 = a4.y + lane_off;
@@ -345,21 +359,47 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) DD_KERNEL(co
         }
         if constexpr (FMT == FMT_TRI) {
           // 8-bit input in 10-bit lanes: lane 2 of the separated sums holds
-          // two pairs, then moves to its 32-bit sum
-          for (int cg = 0; cg < cc; cg += 16) {
-            pair8(cg);
-            if (cc > 8) pair8(cg + 8);
+          // four groups (two pairs), then moves to its 32-bit sum
+          auto moved = [&]() {
 #pragma unroll
             for (int i = 0; i < DPW; ++i)
 #pragma unroll
               for (int j = 0; j < K; ++j) acc[i][j].flush1();
+          };
+          int cg = 0;
+          for (; cg + 16 <= cc; cg += 16) {
+            pair8(cg);
+            pair8(cg + 8);
+            moved();
+          }
+          if (cg < cc) {
+            // 4, 8 or 12 channels left: at most three groups, then the move
+            if (cg + 8 <= cc) {
+              pair8(cg);
+              cg += 8;
+            }
+            if (cg < cc) {
+              // one group of four channels
+#pragma unroll
+              for (int i = 0; i < DPW; ++i) {
+                const uint4 a4 = *reinterpret_cast<const uint4*>(sa + (warp * DPW + i) * cc + cg);
+                const uint32_t q0 = a4.x + lane_off, q1 = a4.y + lane_off;
+                const uint32_t q2 = a4.z + lane_off, q3 = a4.w + lane_off;
+#pragma unroll
+                for (int j = 0; j < K; ++j)
+                  acc[i][j].add4(lds32(q0 + 128u * j), lds32(q1 + 128u * j),
+                                 lds32(q2 + 128u * j), lds32(q3 + 128u * j));
+              }
+            }
+            moved();
           }
         }
       } else
       for (int cg = 0; cg < cc; cg += 4) {
 #pragma unroll
         for (int i = 0; i < DPW; ++i) {
-          const uint4 a4 = *reinterpret_cast<const uint4*>(sa + ((warp * DPW + i) << cc_log) + cg);
+          const uint4 a4 = *reinterpret_cast<const uint4*>(
+              sa + (FINE ? (warp * DPW + i) * cc : (warp * DPW + i) << cc_log) + cg);
           const uint32_t q0 = a4.x + lane_off, q1 = a4.y + lane_off;
           const uint32_t q2 = a4.z + lane_off, q3 = a4.w + lane_off;
 #pragma unroll

@@ -174,6 +174,29 @@ def test_scrunch_input_rows_and_validation(orc):
     assert p.input_rows(G) == G + p.max_delay
 
 
+def _smem_bytes(cc, nww, spw, B=32):
+    """Two staging buffers of cc channels: landing windows (nww + 4 words),
+    the spw - 1 shifted copies (nww words each) and B x cc offsets, plus the
+    two 8-byte barriers."""
+    return 16 + 4 * 2 * (cc * (nww + 4) + cc * (spw - 1) * nww + B * cc)
+
+
+def _check_chunks(cc, nww, spw, nchan=1024, cap=32, B=32):
+    """Each block's chunk fits and is the largest that does: a power of two,
+    or for 8-bit input (three samples a word) a multiple of 4 that stages
+    the band in as few chunks as the largest fitting multiple of 4."""
+    sizes = range(4, cap + 1, 4) if spw == 3 else [4, 8, 16, 32]
+    for c, n in zip(cc.tolist(), nww.tolist()):
+        assert c in sizes and c <= cap and c * B <= 2 * 512
+        assert _smem_bytes(c, n, spw, B) <= 220 * 1024
+        fit = max(f for f in sizes if f <= cap and
+                  _smem_bytes(f, n, spw, B) <= 220 * 1024 and f * B <= 2 * 512)
+        if spw == 3:
+            assert -(-nchan // c) == -(-nchan // fit) and c <= fit
+        else:
+            assert c == fit
+
+
 def test_chunk_geometry_per_trial_block():
     """The staging tables give each trial block its own chunk: as many
     channels (a power of two up to the tiling's cap) as its windows leave
@@ -181,10 +204,11 @@ def test_chunk_geometry_per_trial_block():
     from synth import configs
     c = configs.SURVEY
     p = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
+    p.set_tuning(32, 32, 4)
     g = p.chunk_geometry(2)
     cc, nww = g["chans_per_chunk"], g["window_words"]
     assert len(cc) == len(nww) >= (p.dm_count + 31) // 32
-    assert set(cc.tolist()) <= {4, 8, 16, 32}
+    _check_chunks(cc, nww, 8)
     assert np.all(nww > 0) and np.all(nww % 4 == 0)
     assert 0 < g["smem_bytes"] <= 220 * 1024
     # the window covers the tile (32 lanes x 4 words) plus the block's spread,
@@ -196,23 +220,33 @@ def test_chunk_geometry_per_trial_block():
     # 64 trials per block: at most 1024 / 64 channels per chunk
     p.set_tuning(64, 32, 2)
     assert max(p.chunk_geometry(2)["chans_per_chunk"]) <= 16
-    # a small band with one narrow window everywhere: one geometry
-    t = dd.Plan(64, 64e-6, 1500.0, -1.0, dms=[float(i) for i in range(101)])
+    # a small band whose trials all have the same (zero) delays: one window
+    # everywhere, so one geometry for the launch
+    t = dd.Plan(64, 64e-6, 1500.0, -1.0, dms=[1e-4 * i for i in range(101)])
     gt = t.chunk_geometry(2)
     assert len(set(gt["chans_per_chunk"].tolist())) == 1
     assert len(set(gt["window_words"].tolist())) == 1
+    # blocks of different windows on such a band: equal windows, equal chunks
+    u = dd.Plan(64, 64e-6, 1500.0, -1.0, dms=[float(i) for i in range(101)])
+    gu = u.chunk_geometry(2)
+    for w in set(gu["window_words"].tolist()):
+        assert len(set(gu["chans_per_chunk"][gu["window_words"] == w].tolist())) == 1
+    _check_chunks(gu["chans_per_chunk"], gu["window_words"], 8, nchan=64)
 
 
 def test_chunk_geometry_8bit_wide_trials():
     """8-bit input keeps three samples per word (and two shifted copies), so
     the highest trials' windows (to DM 2000) leave room for only 4 channels
-    per chunk, the lowest for 16."""
+    per chunk and the lowest for many more."""
     from synth import configs
     c = configs.SURVEY
     p = dd.Plan(c["nchans"], c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=2000.0))
+    p.set_tuning(32, 32, 8)
     g = p.chunk_geometry(8)
     cc = g["chans_per_chunk"]
-    assert cc[0] == 16 and cc[int(np.argmax(g["window_words"]))] == 4 and cc.min() == 4
+    _check_chunks(cc, g["window_words"], 3)
+    assert cc[0] >= 16 and cc[int(np.argmax(g["window_words"]))] == 4 and cc.min() == 4
+    assert any(c % 8 == 4 and c > 4 for c in cc.tolist())  # 12, 20 or 28 channels
     with pytest.raises(dd.DedispError):
         p.chunk_geometry(3)
 
