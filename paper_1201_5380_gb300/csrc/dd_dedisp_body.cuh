@@ -29,9 +29,9 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) DD_KERNEL(co
 
   // Chunk geometry and the staging layout it implies: the launch's, set up
   // once here, or (PBG) each trial block's, set up per work item.
-  // FINE: the chunk size is any multiple of 4 (8-bit input, three samples a
-  // word); otherwise a power of two
-  constexpr bool FINE = FMT == FMT_TRI;
+  // FINE: the chunk size is any multiple of 4 (4- and 8-bit input: 8-bit and
+  // 10-bit lanes); otherwise a power of two
+  constexpr bool FINE = FMT == FMT_TRI || FMT == FMT_BYTE;
   struct Geo {
     int cc, cc_log, nww, nwl, buf_words, n_entries, tpc_log, bc;
     int tpc = 0, bq = 0;  // FINE: builder threads per channel, this thread's index among them

@@ -155,8 +155,8 @@ struct SegSpec {
 // lane-shifted copy kap = o mod SPW from word o / SPW, o = kPad + s_i -
 // woff*SPW.  Each block gets its own chunk geometry: its window width nww
 // is the widest read span of its channels, and its chunk the most channels
-// (a power of two up to cc_cap; for 8-bit input a multiple of 4, evened out
-// over the chunks it takes) whose two staging buffers fit in shared memory,
+// (a power of two up to cc_cap; for 4- and 8-bit input a multiple of 4,
+// evened out over the chunks it takes) whose two staging buffers fit in shared memory,
 // so blocks with a small delay spread stage more channels per barrier than
 // the launch's widest block could.  When every block gets the same chunk, all
 // of them take the window width nww_uniform instead (at least the widest
@@ -210,12 +210,13 @@ static dd_status build_stage_tab(const TabSrc& src, int fmt, int cfg, int cc_cap
       if (widest > INT_MAX / 64) return DD_ERR_INVALID_ARG;
       const int nww = (int)((widest + 3) & ~3);
       int cc = cc_cap;
-      if (fmt == FMT_TRI) {
-        // 8-bit input (three samples a word): any multiple of 4 channels,
-        // evened out over the chunks it takes (a smaller last chunk stages
-        // fewer absent channels).  On the 1024-channel band to DM 2000 this
-        // took 41.4 against 42.5 ms; the other formats keep powers of two
-        // (the survey band: 18.08 against 18.00 ms with multiples of 4).
+      if (fmt == FMT_TRI || fmt == FMT_BYTE) {
+        // 4- and 8-bit input (8- and 10-bit lanes): any multiple of 4
+        // channels, evened out over the chunks it takes (a smaller last
+        // chunk stages fewer absent channels).  On the 1024-channel band to
+        // DM 2000 this took 41.4 against 42.5 ms (8-bit) and 31.6 against
+        // 32.2 ms (4-bit); the other formats keep powers of two (the survey
+        // band: 18.08 against 18.00 ms with multiples of 4).
         while (cc > 4 && !fits(cc, nww)) cc -= 4;
         const int nch = (src.nchan + cc - 1) / cc;
         cc = std::min(cc, ((src.nchan + nch - 1) / nch + 3) & ~3);

@@ -132,9 +132,10 @@ constexpr size_t kStatusBytes = 8 + 8 * kItemCounters;
 struct TileCfg {
   int nwarp, dpw, k;  // warps per block, trials per warp, words per lane
 };
-// (16, 2, 8) is for the narrow-accumulator formats (8-bit and wider input,
-// where a wide window over a short tile makes staging dominate); the 4- and
-// 8-bit-lane formats compile it too but spill.  (16, 2, 16) is compiled only
+// (16, 2, 8) is for the narrow-accumulator formats (4-bit and wider input,
+// where a wide window over a short tile makes staging dominate); the
+// 4-bit-lane format compiles it too but spills, as do the 8-bit lanes with
+// 32-bit accumulators.  (16, 2, 16) is compiled only
 // for the one- and two-sample-a-word formats (16-bit lanes, 32-bit words),
 // whose accumulators take one or two registers a word: short work items
 // (the sub-band method's second stage) gain most from its longer tiles.
