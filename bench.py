@@ -147,8 +147,8 @@ class ClockSampler:
 # 2^17 output samples, from ncu, per (input bits, largest trial DM), with the
 # summary that holds the capture; the traffic grows in proportion to the gulp.
 DEDISP_TRAFFIC_2E17 = {
-    (2, 1000.0): (77.300480e6 + 568.200704e6, "profiles/k_dedisp_survey_ncu_full.md"),
-    (8, 2000.0): (222.129408e6 + 712.106240e6, "profiles/k_dedisp_8bit_dm2000_ncu_full.md"),
+    (2, 1000.0): (77.658112e6 + 568.540928e6, "profiles/k_dedisp_survey_ncu_full.md"),
+    (8, 2000.0): (222.201344e6 + 712.811520e6, "profiles/k_dedisp_8bit_dm2000_ncu_full.md"),
     (32, 2000.0): (6154.482e6 + 747.101184e6, "profiles/k_dedisp_f32_dm2000_ncu_full.md"),
 }
 
