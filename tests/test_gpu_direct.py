@@ -318,3 +318,21 @@ def test_sixteen_word_tile_only_for_one_or_two_samples_a_word(orc):
     with pytest.raises(dd.DedispError) as e:
         run_direct(plan, x2, 2, nsamps)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("nbits", [4, 8])
+def test_chunks_of_any_multiple_of_four_channels(orc, nbits):
+    """4- and 8-bit input stage each trial block in chunks of any multiple of
+    4 channels.  On 1000 channels with every trial to DM 2000 the blocks
+    take chunks of 4 up to 28 channels, several of which leave a partial
+    last chunk (absent channels read the zero window); every row compared
+    with the oracle."""
+    c = configs.SURVEY
+    plan = dd.Plan(1000, c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=2000.0))
+    cc = set(plan.chunk_geometry(nbits)["chans_per_chunk"].tolist())
+    assert any(x % 8 == 4 for x in cc) and any(1000 % x for x in cc), cc
+    nsamps = 2311
+    rows = nsamps + plan.max_delay
+    x = synth.uniform_packed(40 + nbits, nbits, rows, 1000, nbits)
+    got, _ = run_direct(plan, x, nbits, nsamps)
+    assert np.array_equal(got, orc.direct(x, nbits, 1000, nsamps, odelays(orc, plan)))
