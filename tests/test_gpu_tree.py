@@ -139,3 +139,20 @@ def test_tree_rejects_trials_beyond_the_diagonal_and_float_input(orc):
     assert e.value.code == 3
     with pytest.raises(dd.DedispError):
         ok.set_tree(12)               # not a power of two
+
+
+@pytest.mark.parametrize("nsub", [32, 64])
+@pytest.mark.parametrize("nbits", [1, 2, 4, 8])
+def test_tree_many_tiles_bit_exact(orc, nsub, nbits):
+    """20011 samples: stage 1 runs 1280 (sub-band, tile) blocks, more than
+    fit on the GPU at once, and stage 2 40 time tiles.  Every trial below the
+    diagonal, full rows, 1- to 8-bit input, with a kill mask."""
+    torch_cuda()
+    mask = np.ones(1024, np.uint8)
+    mask[[3, 64, 65, 511, 1000]] = 0
+    plan = _survey_tree_plan(orc, nsub, mask)
+    nsamps = 20011
+    x = synth.uniform_packed(190 + nbits, nbits, plan.input_rows(nsamps, tree=True), 1024, nbits)
+    got = _run_tree(plan, x, nbits, nsamps)
+    ref = orc.tree_piecewise(x, nbits, 1024, nsub, nsamps, _ext(orc, plan), mask)
+    assert np.array_equal(got, ref), np.argwhere(got != ref)[:5]
