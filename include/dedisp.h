@@ -191,14 +191,16 @@ dd_status dd_plan_get_input_rows(dd_plan plan, int64_t nsamps_out, unsigned flag
 
 /* Kernel tiling: trials per thread block (16, 32 or 64), the most channels
  * staged per pass (4, 8, 16 or 32; default 32: each trial block stages as
- * many as its windows leave room for in shared memory) and output words per
+ * many as its windows leave room for in shared memory, a power of two, or
+ * for 4- and 8-bit input any multiple of 4) and output words per
  * lane (2, 4, 8 or 16; compiled shapes: 32x4, 64x2, 16x4, 32x2, 32x8 and
  * 32x16 trials x words, the last only where the staged image holds one or
  * two samples a word: float input and the sub-band method's second stage;
  * an execute whose staged format lacks the shape returns DD_ERR_INVALID_ARG).  0
  * keeps the current value.  words_per_lane < 0 (the default) picks it per
  * staged format: 16 for one or two samples a word (float input, 16-bit
- * lanes), 8 for 8-bit input (three samples a word), 4 for 1/2/4-bit input.
+ * lanes), 8 for 4- and 8-bit input (8- and 10-bit lanes), 4 for 1- and
+ * 2-bit input.
  * The autotuner below sets all three for the format it is given.
  * dd_plan_get_tuning reports 0 words per lane while it is chosen per
  * format. */
@@ -212,8 +214,10 @@ dd_status dd_plan_get_tuning(dd_plan plan, int *dms_per_block, int *chans_per_ch
  * number of trial blocks, and per block the channels staged per chunk and
  * the window width in 32-bit words, then the launch's dynamic shared
  * memory (its widest block's).  Each block stages as many channels (a power
- * of two, 4 to the tiling's chunk cap) as its two staging buffers allow in
- * shared memory; when all blocks get the same number they share one width.
+ * of two, 4 to the tiling's chunk cap; for 4- and 8-bit input any multiple
+ * of 4, evened out over the chunks it takes) as its two staging buffers
+ * allow in shared memory; when all blocks get the same number they share
+ * one width.
  * Pass null arrays to get n_blocks only; the arrays hold n_blocks entries. */
 dd_status dd_plan_get_chunk_geometry(dd_plan plan, int in_nbits, int32_t *n_blocks,
                                      int32_t *chans_per_chunk, int32_t *window_words,
