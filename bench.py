@@ -141,6 +141,48 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def output_copy_rates(h_out, out, G):
+    """Device-to-host rates of the step's output into the end-to-end leg's
+    own pinned buffer, with no kernels running: one contiguous copy, and the
+    host path's eight pitched copies of its time parts (all rows of columns
+    [c0, c1), parts ending at 16, 32, 48, 64, 80, 90, 96 and 100 % of the
+    gulp).  Beside the 1 GiB link rates they tell a slow link from slow
+    pitched copies on a box whose end-to-end step runs long."""
+    import ctypes
+    import torch
+    try:
+        rt = ctypes.CDLL("libcudart.so")
+    except OSError:
+        return {"output_1d_gbs": None, "output_parts_2d_gbs": None}
+    f = rt.cudaMemcpy2DAsync
+    f.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
+                  ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    esz = out.element_size()
+    rows, pitch = out.shape[0], out.stride(0) * esz
+    nbytes = rows * G * esz
+    st = torch.cuda.current_stream()
+    rates = {}
+    for name in ("output_1d_gbs", "output_parts_2d_gbs"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if name == "output_1d_gbs":
+            h_out.copy_(out, non_blocking=True)
+        else:
+            c0 = 0
+            for e in (160, 320, 480, 640, 800, 900, 960, 1000):
+                c1 = G * e // 1000
+                r = f(h_out.data_ptr() + c0 * esz, pitch, out.data_ptr() + c0 * esz, pitch,
+                      (c1 - c0) * esz, rows, 2, st.cuda_stream)
+                if r != 0:
+                    return {"output_1d_gbs": rates.get("output_1d_gbs"),
+                            "output_parts_2d_gbs": None}
+                c0 = c1
+        torch.cuda.synchronize()
+        rates[name] = nbytes / (time.perf_counter() - t0) / 1e9
+    return rates
+
+
 # ------------------------------------------------------------ cpu oracle
 
 # DRAM bytes (read + write) of one dedispersion launch on the survey band at
@@ -964,6 +1006,7 @@ def run_ours(a, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         link[name + "_gbs"] = 3 * (1 << 30) / (time.perf_counter() - t0) / 1e9
     del hb, db
+    link.update(output_copy_rates(h_out, out, G))
     if not np.array_equal(hout.view(np.uint32)[:, :64],
                           out[:, :64].cpu().numpy().view(np.uint32), equal_nan=False):
         raise RuntimeError("host-path output differs from device-path output")
