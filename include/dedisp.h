@@ -286,18 +286,27 @@ dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void *in, int in_nb
  * file-scope device array of DD_NOALLOC_SCRATCH_BYTES, which every GPU that
  * loads the library holds until the process exits; the call itself allocates
  * and frees nothing.  The first call on a device looks up the array's device
- * address (set-up); make that first call before any stream capture.
+ * address (set-up).  No call may be captured in a CUDA graph: each copies
+ * its tables and kill mask from pageable host memory.
  * Returns DD_ERR_OOM, before launching anything, when the staged image and
  * tables need more than the array (the image takes about nchans *
  * (nsamps_out + max_delay) bytes per staged sample: half a byte for 1- and
  * 2-bit input, 1, 2 or 4 bytes for 4-bit, 8-bit or float input).
  * All calls share the array and each starts by reloading it: calls whose work
  * overlaps on the GPU (other streams or threads) race, so the caller must
- * serialise them.  Bound flags of this call are not reported by
- * dd_plan_get_device_status. */
+ * serialise them.  Its device-side bound flags are read with
+ * dd_noalloc_get_device_status, not dd_plan_get_device_status. */
 dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const void *in_dev,
                              int in_nbits, int64_t in_row_stride_bytes, void *out_dev,
                              int64_t out_row_stride_elems, void *cuda_stream);
+/* The device-side bound flags (the dd_plan_get_device_status bits) of the
+ * latest dd_execute_noalloc call on the current device: waits for
+ * cuda_stream (the stream that call used; NULL = the legacy default stream)
+ * to finish, then copies the 4-byte status word out of the scratch array.
+ * It allocates and frees nothing and does not clear the word (the next
+ * call resets it); 0 = clean.  DD_ERR_INVALID_ARG when flags is NULL;
+ * CUDA errors of the wait or the copy are returned as their dd_status. */
+dd_status dd_noalloc_get_device_status(void *cuda_stream, uint32_t *flags);
 
 /* ---- streaming: consecutive gulps of one beam (the overlap of Eq. 2) */
 

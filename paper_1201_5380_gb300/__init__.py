@@ -73,6 +73,7 @@ def _load_lib():
         "dd_plan_reset_kernel_timing": (I, [P]),
         "dd_execute": (I, [P, I64, P, I, I64, P, I64, P, ctypes.c_uint]),
         "dd_execute_noalloc": (I, [P, I64, P, I, I64, P, I64, P]),
+        "dd_noalloc_get_device_status": (I, [P, pp(ctypes.c_uint32)]),
         "dd_plan_set_tree": (I, [P, I]),
         "dd_plan_get_tree_dm_limit": (I, [P, I, pp(D)]),
         "dd_server_set_timeout": (I, [P, D]),
@@ -383,6 +384,15 @@ def execute_noalloc(plan, inp, nbits, nsamps_out, out, stream=None):
                                    op, int(ostride // 4), _stream_ptr(stream)),
            "dd_execute_noalloc")
     return out
+
+
+def noalloc_device_status(stream=None):
+    """dd_noalloc_get_device_status: the bound flags of the latest
+    execute_noalloc call on the current device, after waiting for `stream`."""
+    v = ctypes.c_uint32(0)
+    _check(_lib.dd_noalloc_get_device_status(_stream_ptr(stream), ctypes.byref(v)),
+           "dd_noalloc_get_device_status")
+    return int(v.value)
 
 
 class Stream:

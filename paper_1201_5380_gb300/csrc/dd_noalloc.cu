@@ -93,7 +93,8 @@ extern "C" dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const 
   s = plan_direct_launch(*p, fmt, fmt == FMT_F32 ? OUT_F32 : OUT_U32, vmax_for_nbits(in_nbits),
                          {j}, &L, &tabs);
   if (s != DD_OK) return s;
-  if (L.lp.n_items == 0) return DD_OK;
+  if (L.lp.n_items == 0)  // nothing to launch: only the status word is reset
+    return cuda_status(cudaMemsetAsync(sc, 0, 16, st));
   const std::shared_ptr<StageTab> t = tabs.at(0);
 
   // Layout of the scratch for this call; reject problems that do not fit.
@@ -141,4 +142,21 @@ extern "C" dd_status dd_execute_noalloc(dd_plan plan, int64_t nsamps_out, const 
   L.lp.status = status;
   L.lp.next_item = reinterpret_cast<unsigned long long*>(sc + off_status + 8);
   return cuda_status(launch_dedisp(L.fmt, L.outk, L.wide, L.cfg, L.lp, L.grid, L.smem, st));
+}
+
+extern "C" dd_status dd_noalloc_get_device_status(void* cuda_stream, uint32_t* flags) {
+  if (!flags) return DD_ERR_INVALID_ARG;
+  *flags = 0;
+  unsigned char* sc = nullptr;
+  dd_status s = scratch_for_current_device(&sc);
+  if (s != DD_OK) return s;
+  // The status word sits at the start of the scratch; each dd_execute_noalloc
+  // call resets it on its stream before its kernels run.
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  uint32_t v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, sc, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  *flags = v;
+  return DD_OK;
 }

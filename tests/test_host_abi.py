@@ -268,3 +268,5 @@ def test_noalloc_rejects_bad_arguments_before_any_device_work():
     assert lib.dd_execute_noalloc(h, 100, buf, 8, ok_stride - 1, buf, 100, None) == 1
     plan.set_output_bits(8)   # scaled output: the call writes uint32 rows only
     assert lib.dd_execute_noalloc(h, 100, buf, 8, ok_stride, buf, 100, None) == 1
+    # the status query checks its pointer before it looks up the scratch
+    assert lib.dd_noalloc_get_device_status(None, None) == 1

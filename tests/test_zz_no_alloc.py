@@ -119,6 +119,8 @@ def test_noalloc_equals_the_oracle_and_allocates_nothing():
         torch.cuda.synchronize()
         assert np.array_equal(outs[k].cpu().numpy().view(np.uint32), ref), k
     assert _call_noalloc(plan, d_ins[0], 2, nsamps, outs[0], torch) == 0
+    # the calls' bound flags, read back from the scratch: clean
+    assert dd.noalloc_device_status(torch.cuda.current_stream()) == 0
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
     assert free1 == free0
