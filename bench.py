@@ -573,10 +573,12 @@ def run_subband(a, x, plan_direct, d_out_direct, G, peak_adds):
                     "value": units / (ms / 1e3) / 1e9, "adds_per_step": adds,
                     "adds_vs_direct": adds / units, "snr_loss": snr,
                     "stages": {
-                        "stage1": {"ms": k1_ms / reps, "adds": adds1, "lanes": "4-bit",
+                        "stage1": {"ms": k1_ms / reps, "adds": adds1,
+                                   "lanes": "4-bit, 8-bit-lane rows out",
                                    "frac_of_int_add_probe": adds1 / (k1_ms / reps / 1e3)
                                    / peak_adds},
-                        "stage2": {"ms": k2_ms / reps, "adds": adds2, "lanes": "16-bit",
+                        "stage2": {"ms": k2_ms / reps, "adds": adds2,
+                                   "lanes": "8-bit pairs of sub-bands into 16-bit sums",
                                    "frac_of_int_add_probe": adds2 / (k2_ms / reps / 1e3)
                                    / peak_adds}}}
         del d_in, out

@@ -33,6 +33,7 @@ template <> struct FmtT<FMT_HALF> { static constexpr int SPW = 2, LW = 16; };
 template <> struct FmtT<FMT_U32> { static constexpr int SPW = 1, LW = 32; };
 template <> struct FmtT<FMT_F32> { static constexpr int SPW = 1, LW = 32; };
 template <> struct FmtT<FMT_TRI> { static constexpr int SPW = 3, LW = 10; };
+template <> struct FmtT<FMT_SB8> { static constexpr int SPW = 4, LW = 8; };
 
 // Word w of a staged row shifted by kap samples (the next word b supplies
 // the samples shifted in): a funnel shift for lanes that fill the word, an
@@ -189,6 +190,30 @@ template <bool WIDE> struct Acc<FMT_HALF, WIDE> {
       v[0] = h & 0xFFFFu;
       v[1] = h >> 16;
     }
+  }
+};
+
+// 8-bit lanes of sub-band stage 2 (FMT_SB8): every staged value is a
+// stage-1 sum below 128, so two sub-bands add lane-parallel without a carry
+// (a pair stays below 256).  Each pair is then spread into 16-bit lanes:
+// e = samples {0,2} (a mask), o = samples {1,3} (a byte permute).  Exact
+// while a trial's total stays below 2^16, which the plan checks; there is
+// no wide variant.
+template <bool WIDE> struct Acc<FMT_SB8, WIDE> {
+  uint32_t e, o;
+  __device__ __forceinline__ void zero() { e = o = 0u; }
+  __device__ __forceinline__ void add4(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
+    const uint32_t a = x0 + x1, c = x2 + x3;
+    e = e + (a & 0x00FF00FFu) + (c & 0x00FF00FFu);
+    // bytes 1 and 3 of the pair into the low bytes of the 16-bit lanes
+    o = o + __byte_perm(a, 0u, 0x4341u) + __byte_perm(c, 0u, 0x4341u);
+  }
+  __device__ __forceinline__ void flush0() {}
+  __device__ __forceinline__ void flush1() {}
+  __device__ __forceinline__ void flush2() {}
+  __device__ __forceinline__ void final(uint32_t v[4]) {
+    v[0] = e & 0xFFFFu; v[2] = e >> 16;
+    v[1] = o & 0xFFFFu; v[3] = o >> 16;
   }
 };
 

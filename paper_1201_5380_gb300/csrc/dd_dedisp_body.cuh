@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) DD_KERNEL(co
     __syncthreads();
 #endif
 
-    // (d) exact sums out: u32 rows, float rows, or 16-bit image rows
+    // (d) exact sums out: u32 rows, float rows, or 16- or 8-bit image rows
 #pragma unroll
     for (int i = 0; i < DPW; ++i) {
       const int slot = warp * DPW + i;
@@ -469,6 +469,13 @@ __global__ void __launch_bounds__(NWARP * 32, (NWARP <= 8 ? 2 : 1)) DD_KERNEL(co
           } else if (SPW == 2) {
             dst[0] = v[0] | (v[1 % SPW] << 16);
           }
+        } else if constexpr (OUTK == OUT_BYTEIMG) {
+          // stage-1 sums below 128 (the plan's check), four to a word
+          static_assert(SPW == 8, "8-bit image rows come from the 4-bit lanes");
+          uint32_t* dst = out_g + (int64_t)(d0 + slot) * S.out_stride + (tw >> 2);
+          *reinterpret_cast<uint2*>(dst) =
+              make_uint2(v[0] | (v[1 % SPW] << 8) | (v[2 % SPW] << 16) | (v[3 % SPW] << 24),
+                         v[4 % SPW] | (v[5 % SPW] << 8) | (v[6 % SPW] << 16) | (v[7 % SPW] << 24));
         } else if (OUTK == OUT_NARROW) {
           // scaled low-bit output: the top out_bits of the sum's range
           const uint32_t cap = (1u << p.out_bits) - 1u;

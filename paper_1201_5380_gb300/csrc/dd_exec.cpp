@@ -126,6 +126,10 @@ static void flush_periods(int fmt, int vmax, int nchan_max, bool* wide, int* f0,
       *f0 = std::max(1, 65535 / (4 * vmax));
       *wide = (int64_t)nchan_max * vmax > 65535;
       break;
+    case FMT_SB8:
+      // pairs of values below 128 spread into 16-bit lanes (no flush)
+      *wide = (int64_t)nchan_max * vmax > 65535;
+      break;
     case FMT_TRI:
       *f0 = 1;  // every group of 4 channels leaves the 10-bit lanes
       *f1 = 4;  // lane 2 of the separated sums holds four groups
@@ -395,6 +399,9 @@ static dd_status finish_launch(Plan& p, const Tuning& tune, int fmt, int outk, i
   // the launch's kernel (scaled output runs the OUT_NARROW kernel)
   const int outk_run = outk == OUT_U32 && p.out_bits < 32 ? OUT_NARROW : outk;
   const bool mt_ok = multi_tile_compiled(fmt, outk_run, wide, cfg);
+  // the 8-bit-lane sub-band stages have the multi-tile kernel only
+  const bool mt_only = multi_tile_only(fmt, outk_run);
+  if (mt_only && !mt_ok) return DD_ERR_INVALID_ARG;
 
   L->fmt = fmt;
   L->outk = outk;
@@ -421,6 +428,9 @@ static dd_status finish_launch(Plan& p, const Tuning& tune, int fmt, int outk, i
   if (L->segs.size() > (size_t)kMaxSegs) return DD_ERR_INVALID_ARG;
   if (outk == OUT_HALFIMG && (wide || (int64_t)nchan_max * std::max(vmax, 1) > 65535))
     return DD_ERR_OVERFLOW;
+  if (outk == OUT_BYTEIMG && (wide || (int64_t)nchan_max * std::max(vmax, 1) > 127))
+    return DD_ERR_OVERFLOW;
+  if (fmt == FMT_SB8 && (wide || 2 * (int64_t)std::max(vmax, 1) > 255)) return DD_ERR_OVERFLOW;
   L->wide = wide;
   LaunchParams& lp = L->lp;
   std::memset(&lp, 0, sizeof(lp));
@@ -430,7 +440,7 @@ static dd_status finish_launch(Plan& p, const Tuning& tune, int fmt, int outk, i
   lp.f1 = f1;
   lp.f2 = f2;
   lp.n_items = items;
-  lp.multi_tile = multi ? 1 : 0;
+  lp.multi_tile = (multi || mt_only) ? 1 : 0;
   lp.vec_out = vec_out ? 1 : 0;
   // scaled low-bit output (Sec. 4.3): keep the top out_bits of the range a
   // sum can reach, nchan * vmax
@@ -787,10 +797,17 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
   }
   if (e != cudaSuccess) return cuda_status(e);
 
-  // intermediate: 16-bit image rows when stage-1 sums fit, else 32-bit
+  // intermediate: 8-bit image rows when stage-1 sums stay below 128 (1- and
+  // 2-bit input; stage 2 then adds two sub-bands a lane and a trial's total
+  // fits 16 bits), else 16-bit rows when they fit, else 32-bit.  The 8-bit
+  // stages are compiled for the default tiles only (stage 1: 32 trials, 4
+  // words a lane; stage 2: 32 trials, 8 words a lane).
   const int64_t vmax1 = (int64_t)Np * vmax_in;
-  const bool half = vmax1 <= 65535;
-  const int fmt2 = half ? FMT_HALF : FMT_U32;
+  const bool byte = fmt == FMT_NIB && vmax1 <= 127 && (int64_t)C * vmax_in <= 65535 &&
+                    p.out_bits == 32 && tile_cfg_index(t1) == 0 &&
+                    tile_cfg_index(tuning_for(p.tune, FMT_SB8)) == 4;
+  const bool half = !byte && vmax1 <= 65535;
+  const int fmt2 = byte ? FMT_SB8 : (half ? FMT_HALF : FMT_U32);
   const int bi = b_index(B);
   const int32_t spread2 = p.sb2_spread_B[bi], lo2 = p.sb2_lo_B[bi];
   if (lo2 > kPad) return DD_ERR_INVALID_ARG;
@@ -830,7 +847,7 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
     g.blk = static_cast<const int32_t*>(p.d_sb1_blk[bi1].p);
     g.n_dmblk = p.sb1_nblk_B[bi1];
     g.nsamps = len1;
-    g.out = S + (half ? kPad / 2 : kPad);
+    g.out = S + kPad / spw2;
     g.out_stride = (int64_t)nsb * rw2;
     sp.kind = 1;
     sp.owner = &p;
@@ -838,7 +855,8 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
                     lo1};
   }
   LaunchPlan L1;
-  s = finish_launch(p, t1, fmt, half ? OUT_HALFIMG : OUT_U32, vmax_in, specs, true, &L1);
+  s = finish_launch(p, t1, fmt, byte ? OUT_BYTEIMG : (half ? OUT_HALFIMG : OUT_U32), vmax_in,
+                    specs, true, &L1);
   if (s != DD_OK) return s;
   if ((s = run_launch(p, L1, a.st)) != DD_OK) return s;
 

@@ -30,11 +30,17 @@ namespace dd {
 //   FMT_F32  32-bit float, 1 sample/word, float input
 //   FMT_TRI  10-bit lanes at bits [0,10), [10,20), [20,30), 3 samples/word,
 //            8-bit input of the direct transform (4 channels fit a lane)
+//   FMT_SB8  8-bit lanes, 4 samples/word: sub-band stage 2 over stage-1
+//            sums below 128 (1- and 2-bit input), two sub-bands a lane
 // ---------------------------------------------------------------------------
-enum Fmt { FMT_NIB = 0, FMT_BYTE = 1, FMT_HALF = 2, FMT_U32 = 3, FMT_F32 = 4, FMT_TRI = 5 };
+enum Fmt {
+  FMT_NIB = 0, FMT_BYTE = 1, FMT_HALF = 2, FMT_U32 = 3, FMT_F32 = 4, FMT_TRI = 5, FMT_SB8 = 6
+};
 // OUT_NARROW: scaled uint8/uint16 rows (LaunchParams::out_bits, out_shift),
 // a separate instantiation so the uint32 kernel's code is untouched.
-enum OutKind { OUT_U32 = 0, OUT_F32 = 1, OUT_HALFIMG = 2, OUT_NARROW = 3 };
+// OUT_HALFIMG / OUT_BYTEIMG: sub-band stage-1 rows written as the stage-2
+// image, in 16-bit (FMT_HALF) or 8-bit (FMT_SB8) lanes.
+enum OutKind { OUT_U32 = 0, OUT_F32 = 1, OUT_HALFIMG = 2, OUT_NARROW = 3, OUT_BYTEIMG = 4 };
 
 constexpr int kPad = 32;  // image samples before time 0 (multiple of 4*SPW)
 
@@ -42,6 +48,7 @@ inline int fmt_spw(int fmt) {
   switch (fmt) {
     case FMT_NIB: return 8;
     case FMT_BYTE: return 4;
+    case FMT_SB8: return 4;
     case FMT_HALF: return 2;
     case FMT_TRI: return 3;
     default: return 1;
@@ -70,7 +77,7 @@ struct Seg {
   const int32_t* delays;  // delay of trial 0, channel 0 (group 0)
   void* out;              // output row of trial 0 at time 0 (group 0)
   int64_t row_words;      // image row pitch, words
-  int64_t out_stride;     // output row pitch (elements, or words for OUT_HALFIMG)
+  int64_t out_stride;     // output row pitch (elements; words for the image outputs)
   int64_t nsamps;         // outputs per trial
   int64_t item_begin;     // first global item index of this segment
   int64_t tile0;          // first time tile of the segment's first item
@@ -151,6 +158,9 @@ cudaError_t dedisp_max_blocks_per_sm(int fmt, int outk, bool wide, int cfg, bool
 // Whether the multi-tile kernel (items of several time tiles) is compiled
 // for this staged format, output kind, accumulator width and tile shape.
 bool multi_tile_compiled(int fmt, int outk, bool wide, int cfg);
+// Whether only the multi-tile kernel is compiled for them (the 8-bit-lane
+// sub-band stages): their launches always take it, one tile an item or more.
+bool multi_tile_only(int fmt, int outk);
 // Image words [w_first, words) of every channel row, in staged format fmt
 // (fmt_for_nbits, or FMT_HALF for 8-bit input of the sub-band method).
 cudaError_t launch_corner_turn(int nbits, int fmt, const uint8_t* in, int64_t in_stride,

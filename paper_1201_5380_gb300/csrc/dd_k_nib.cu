@@ -16,11 +16,14 @@ cudaError_t dispatch_nib(int outk, bool wide, int cfg, bool pbg, const LaunchPar
   return cudaErrorInvalidValue;
 }
 
-// Multi-tile items: 2-bit sub-band stage 1 (16-bit image output), tile 0.
+// Multi-tile items: 1- and 2-bit sub-band stage 1 (16- or 8-bit image
+// output), tile 0.  The 8-bit image is written by this kernel only.
 cudaError_t dispatch_nib_mt(int outk, bool wide, int cfg, bool pbg, const LaunchParams* p,
                             int grid, size_t smem, cudaStream_t st, int* occ) {
   if (outk == OUT_HALFIMG && !wide && cfg == 0)
     return dispatch_mt<FMT_NIB, OUT_HALFIMG, false, 0>(pbg, p, grid, smem, st, occ);
+  if (outk == OUT_BYTEIMG && !wide && cfg == 0)
+    return dispatch_mt<FMT_NIB, OUT_BYTEIMG, false, 0>(pbg, p, grid, smem, st, occ);
   return cudaErrorInvalidValue;
 }
 

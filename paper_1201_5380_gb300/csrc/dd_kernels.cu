@@ -21,12 +21,17 @@ cudaError_t dispatch_nib_mt(int, bool, int, bool, const LaunchParams*, int, size
                             int*);
 cudaError_t dispatch_half_mt(int, bool, int, bool, const LaunchParams*, int, size_t,
                              cudaStream_t, int*);
+cudaError_t dispatch_sb8_mt(int, bool, int, bool, const LaunchParams*, int, size_t,
+                            cudaStream_t, int*);
 
 bool multi_tile_compiled(int fmt, int outk, bool wide, int cfg) {
-  if (fmt == FMT_NIB) return outk == OUT_HALFIMG && !wide && cfg == 0;
+  if (fmt == FMT_NIB) return (outk == OUT_HALFIMG || outk == OUT_BYTEIMG) && !wide && cfg == 0;
   if (fmt == FMT_HALF) return cfg == 5 && ((outk == OUT_HALFIMG && !wide) || outk == OUT_U32);
+  if (fmt == FMT_SB8) return cfg == 4 && outk == OUT_U32 && !wide;
   return false;
 }
+
+bool multi_tile_only(int fmt, int outk) { return fmt == FMT_SB8 || outk == OUT_BYTEIMG; }
 
 static cudaError_t dispatch(int fmt, int outk, bool wide, int cfg, bool pbg, bool mt,
                             const LaunchParams* p, int grid, size_t smem, cudaStream_t st,
@@ -34,8 +39,10 @@ static cudaError_t dispatch(int fmt, int outk, bool wide, int cfg, bool pbg, boo
   if (mt) {
     if (fmt == FMT_NIB) return dispatch_nib_mt(outk, wide, cfg, pbg, p, grid, smem, st, occ);
     if (fmt == FMT_HALF) return dispatch_half_mt(outk, wide, cfg, pbg, p, grid, smem, st, occ);
+    if (fmt == FMT_SB8) return dispatch_sb8_mt(outk, wide, cfg, pbg, p, grid, smem, st, occ);
     return cudaErrorInvalidValue;
   }
+  if (multi_tile_only(fmt, outk)) return cudaErrorInvalidValue;
   switch (fmt) {
     case FMT_NIB: return dispatch_nib(outk, wide, cfg, pbg, p, grid, smem, st, occ);
     case FMT_BYTE: return dispatch_byte(outk, wide, cfg, pbg, p, grid, smem, st, occ);

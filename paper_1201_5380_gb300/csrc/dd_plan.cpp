@@ -297,9 +297,11 @@ Tuning tuning_for(const Tuning& t, int fmt) {
   // words per lane by accumulator width: 16 where a word's sums take one or
   // two registers (16-bit lanes, 32-bit words), 8 for the 10- and 8-bit
   // lanes' three registers a word (4-bit input on the 1024-channel band to
-  // DM 2000, 2^19: 31.6 against 38.3 ms at 4), 4 for the 4-bit lanes' seven
+  // DM 2000, 2^19: 31.6 against 38.3 ms at 4) and for the sub-band stage 2's
+  // 8-bit lanes (16 words a lane are compiled for two samples a word at
+  // most), 4 for the 4-bit lanes' seven
   const bool one_two = fmt == FMT_HALF || fmt == FMT_U32 || fmt == FMT_F32;
-  const bool three = fmt == FMT_TRI || fmt == FMT_BYTE;
+  const bool three = fmt == FMT_TRI || fmt == FMT_BYTE || fmt == FMT_SB8;
   const int prefs[4] = {one_two ? 16 : (three ? 8 : 4), one_two ? 8 : 4, 4, 2};
   for (int k : prefs)
     if (have_tile_cfg(t.dms_per_block, k)) {

@@ -45,7 +45,11 @@ def test_subband_centred_alignment_bit_exact(orc, centred):
         assert np.array_equal(got[gn], di[gn])
 
 
-@pytest.mark.parametrize("nsub,ndmn,nbits", [(16, 8, 2), (64, 16, 4), (32, 5, 8), (8, 32, 1)])
+# 1- and 2-bit input with stage-1 sums below 128 (16 x 3, 8 x 1) takes the
+# 8-bit-lane intermediate; 64 x 3 and 128 x 1 take 16-bit lanes, as do 4- and
+# 8-bit input
+@pytest.mark.parametrize("nsub,ndmn,nbits", [(16, 8, 2), (64, 16, 4), (32, 5, 8), (8, 32, 1),
+                                             (64, 16, 2), (128, 8, 1)])
 def test_subband_shapes_bit_exact(orc, nsub, ndmn, nbits):
     plan = _plan(step=8, nsub=nsub, ndmn=ndmn)
     nsamps = 1300
@@ -53,6 +57,43 @@ def test_subband_shapes_bit_exact(orc, nsub, ndmn, nbits):
     x = synth.uniform_packed(22, nbits, rows, 1024, nbits)
     got, _ = run_direct(plan, x, nbits, nsamps, subband=True)
     ref = orc.subband(x, nbits, 1024, nsub, ndmn, odelays(orc, plan), nsamps)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("nchans,nsub,nbits", [(1008, 42, 2), (1016, 127, 1), (1032, 43, 2)])
+def test_subband_stage1_sums_at_the_8bit_image_limit(orc, nchans, nsub, nbits):
+    """Stage-1 sums of nsub channels reach nsub * (2^nbits - 1): 126 and 127,
+    the largest the 8-bit-lane intermediate takes (stage 2 adds two of them
+    in a byte lane), and 129, one past it (16-bit lanes).  Runs of saturated
+    input rows alternate with uniform noise, so the largest sums sit beside
+    ordinary ones in the same words."""
+    c = configs.SUBBAND
+    full = dd.Plan(nchans, c["dt"], c["f0"], c["df"], dm_rule=dict(lo=0.0, hi=1000.0))
+    plan = dd.Plan(nchans, c["dt"], c["f0"], c["df"], dms=full.dms[::10], subband=(nsub, 16))
+    nsamps = 2100
+    rows = nsamps + plan.subband_max_delay
+    x = synth.uniform_packed(41, nbits, rows, nchans, nbits)
+    assert (nchans * nbits) % 8 == 0  # no spare bits in a row
+    x[(np.arange(rows) // 300) % 2 == 0] = 0xFF
+    got, _ = run_direct(plan, x, nbits, nsamps, subband=True)
+    ref = orc.subband(x, nbits, nchans, nsub, 16, odelays(orc, plan), nsamps)
+    assert ref.max() == nchans * ((1 << nbits) - 1)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("tuning", [(32, 16, 0), (32, 0, 4), (64, 0, 0)])
+def test_subband_tilings_bit_exact(orc, tuning):
+    """Tilings besides the default: 16-channel chunks (8-bit-lane stages with
+    smaller chunks), 4 words a lane and 64-trial blocks (both stages then run
+    16-bit lanes, the 8-bit-lane stages being compiled for the default tile
+    shapes only)."""
+    plan = _plan(step=8)
+    plan.set_tuning(*tuning)
+    nsamps = 1900
+    rows = nsamps + plan.subband_max_delay
+    x = synth.uniform_packed(26, 0, rows, 1024, 2)
+    got, _ = run_direct(plan, x, 2, nsamps, subband=True)
+    ref = orc.subband(x, 2, 1024, 32, 32, odelays(orc, plan), nsamps)
     assert np.array_equal(got, ref)
 
 
