@@ -128,7 +128,12 @@ dd_status dd_plan_set_killmask(dd_plan plan, const uint8_t *mask);
 dd_status dd_plan_set_gulp(dd_plan plan, int64_t gulp_samples);
 
 /* Enable the sub-band method of Sec. 4.1: chans_per_subband (N') must
- * divide nchans; dms_per_nominal (N'_DM) >= 1.  0, 0 disables it. */
+ * divide nchans; dms_per_nominal (N'_DM) >= 1.  0, 0 disables it.
+ * The stage-1 sums are kept on the device in 8-bit lanes for 1- and 2-bit
+ * input when N' * (2^nbits - 1) < 128 and nchans * (2^nbits - 1) < 2^16
+ * under the default tiling (dms_per_block 32, words per lane chosen per
+ * format), else in 16-bit lanes when N' * max sample < 2^16, else in 32-bit
+ * words.  Results are exact in every case. */
 dd_status dd_plan_set_subband(dd_plan plan, int chans_per_subband,
                               int dms_per_nominal);
 
