@@ -10,7 +10,9 @@
 // every step there between two buffers, and writes only the trails stage 2
 // reads (d' up to the largest d'_n(d) of the sub-band).  Samples are 16-bit
 // lanes, two per 32-bit word, so one add serves two samples: a sub-band's
-// sums (N' * max sample) stay below 2^16.
+// sums (N' * max sample) stay below 2^16.  Where they stay below 128 (1- and
+// 2-bit input, N' * max sample < 128) the trails are written in 8-bit lanes,
+// four samples a word, and stage 2 reads half the words.
 //
 // Step i (radix r = 2^i), Eq. (tree_algorithm_first .. last):
 //   A'[2v + j][t] = A[Phi(r, 2v)][t] + A[Phi(r, 2v + 1)][t + Theta(i, 2v + j)]
@@ -47,7 +49,7 @@ struct TreeS1 {
   int64_t in_stride;      // bytes per row
   int64_t in_rows;        // valid rows (zeros beyond)
   const uint8_t* mask;    // nchans, 0 = killed
-  uint32_t* S;            // stage-1 rows, two 16-bit samples per word
+  uint32_t* S;            // stage-1 rows: two 16-bit or (OUT8) four 8-bit samples a word
   int64_t s_pitch;        // words per S row
   const int32_t* roff;    // first S row of each sub-band (+ end)
   int nbits;
@@ -76,38 +78,70 @@ __device__ __forceinline__ uint32_t half_shift(uint32_t w0, uint32_t w1) {
 // block of 4R rows, output K = 4m + sub takes trail m of its four quarters
 // j = 0..3, quarter j shifted by j*m plus 0, sub/2, (sub+1)/2, sub samples
 // (j = 0, 1, 2, 3): the composition of the two steps' Theta and Phi.
-template <int NSUB, int R, bool LAST>
+// Word q of outputs 4g .. 4g + 3 (g = sb * R + m) into r.
+template <int NSUB, int R>
+__device__ __forceinline__ void radix4_words(const uint32_t* src, int sb, int m, int q,
+                                             uint32_t (&r)[4]) {
+  constexpr int PW = tree_pitch(NSUB);
+  const uint32_t* q0 = src + ((4 * sb + 0) * R + m) * PW + q;
+  const uint32_t* q1 = src + ((4 * sb + 1) * R + m) * PW + q + (m >> 1);
+  const uint32_t* q2 = src + ((4 * sb + 2) * R + m) * PW + q + m;
+  const uint32_t* q3 = src + ((4 * sb + 3) * R + m) * PW + q + ((3 * m) >> 1);
+  const int ps = (m & 1) * 16;  // quarters 1 and 3 start on an odd sample when m is odd
+  const uint32_t a = q0[0];
+  const uint32_t b0 = __funnelshift_r(q1[0], q1[1], ps), b1 = __funnelshift_r(q1[1], q1[2], ps);
+  const uint32_t c0 = q2[0], c1 = q2[1];
+  const uint32_t d0 = __funnelshift_r(q3[0], q3[1], ps), d1 = __funnelshift_r(q3[1], q3[2], ps);
+  const uint32_t d2 = __funnelshift_r(q3[2], q3[3], ps);
+  const uint32_t b_1 = half_shift(b0, b1), c_1 = half_shift(c0, c1);
+  r[0] = a + b0 + c0 + d0;
+  r[1] = a + b0 + c_1 + half_shift(d0, d1);
+  r[2] = a + b_1 + c_1 + d1;
+  r[3] = a + b_1 + c1 + half_shift(d1, d2);
+}
+
+// The last pass of a tile writes the trails to global memory: as 16-bit
+// lanes (one word of the pass per word), or (OUT8) as 8-bit lanes, four
+// samples a word made of two adjacent words of the pass by one byte
+// permute (bytes 0 and 2 of each: the sums are below 128).
+__device__ __forceinline__ uint32_t pack_bytes(uint32_t lo, uint32_t hi) {
+  return __byte_perm(lo, hi, 0x6420u);
+}
+
+template <int NSUB, int R, bool LAST, bool OUT8>
 __device__ __forceinline__ void tree_radix4(const uint32_t* src, uint32_t* dst, const TreeOut& o) {
   constexpr int T = tree_tile(NSUB), WW = tree_words(NSUB), PW = tree_pitch(NSUB);
-  constexpr int QN = LAST ? T / 2 : WW;  // the last pass writes only the tile
-  for (int e = threadIdx.x; e < (NSUB / 4) * QN; e += kTreeThreads) {
-    const int g = e / QN;
-    const int q = e - g * QN;
-    const int sb = g / R, m = g % R;
-    const int o0 = 4 * g;
-    if (LAST && o0 >= o.nrow) continue;
-    const uint32_t* q0 = src + ((4 * sb + 0) * R + m) * PW + q;
-    const uint32_t* q1 = src + ((4 * sb + 1) * R + m) * PW + q + (m >> 1);
-    const uint32_t* q2 = src + ((4 * sb + 2) * R + m) * PW + q + m;
-    const uint32_t* q3 = src + ((4 * sb + 3) * R + m) * PW + q + ((3 * m) >> 1);
-    const int ps = (m & 1) * 16;  // quarters 1 and 3 start on an odd sample when m is odd
-    const uint32_t a = q0[0];
-    const uint32_t b0 = __funnelshift_r(q1[0], q1[1], ps), b1 = __funnelshift_r(q1[1], q1[2], ps);
-    const uint32_t c0 = q2[0], c1 = q2[1];
-    const uint32_t d0 = __funnelshift_r(q3[0], q3[1], ps), d1 = __funnelshift_r(q3[1], q3[2], ps);
-    const uint32_t d2 = __funnelshift_r(q3[2], q3[3], ps);
-    const uint32_t b_1 = half_shift(b0, b1), c_1 = half_shift(c0, c1);
-    uint32_t r[4];
-    r[0] = a + b0 + c0 + d0;
-    r[1] = a + b0 + c_1 + half_shift(d0, d1);
-    r[2] = a + b_1 + c_1 + d1;
-    r[3] = a + b_1 + c1 + half_shift(d1, d2);
+  if constexpr (LAST && OUT8) {
+    constexpr int QN = T / 4;
+    for (int e = threadIdx.x; e < (NSUB / 4) * QN; e += kTreeThreads) {
+      const int g = e / QN;
+      const int q = e - g * QN;
+      const int o0 = 4 * g;
+      if (o0 >= o.nrow) continue;
+      uint32_t ra[4], rb[4];
+      radix4_words<NSUB, R>(src, g / R, g % R, 2 * q, ra);
+      radix4_words<NSUB, R>(src, g / R, g % R, 2 * q + 1, rb);
 #pragma unroll
-    for (int sub = 0; sub < 4; ++sub) {
-      if (LAST) {
-        if (o0 + sub < o.nrow) o.S[(int64_t)(o.r0 + o0 + sub) * o.s_pitch + q] = r[sub];
-      } else {
-        dst[(o0 + sub) * PW + q] = r[sub];
+      for (int sub = 0; sub < 4; ++sub)
+        if (o0 + sub < o.nrow)
+          o.S[(int64_t)(o.r0 + o0 + sub) * o.s_pitch + q] = pack_bytes(ra[sub], rb[sub]);
+    }
+  } else {
+    constexpr int QN = LAST ? T / 2 : WW;  // the last pass writes only the tile
+    for (int e = threadIdx.x; e < (NSUB / 4) * QN; e += kTreeThreads) {
+      const int g = e / QN;
+      const int q = e - g * QN;
+      const int o0 = 4 * g;
+      if (LAST && o0 >= o.nrow) continue;
+      uint32_t r[4];
+      radix4_words<NSUB, R>(src, g / R, g % R, q, r);
+#pragma unroll
+      for (int sub = 0; sub < 4; ++sub) {
+        if (LAST) {
+          if (o0 + sub < o.nrow) o.S[(int64_t)(o.r0 + o0 + sub) * o.s_pitch + q] = r[sub];
+        } else {
+          dst[(o0 + sub) * PW + q] = r[sub];
+        }
       }
     }
   }
@@ -116,49 +150,74 @@ __device__ __forceinline__ void tree_radix4(const uint32_t* src, uint32_t* dst, 
 // One step (radix R = 2^i): outputs 2v and 2v + 1 take row lo and row hi = lo
 // + R of their block of 2R rows, hi shifted by s = v mod R and s + 1
 // samples (Theta of Eq. tree_integer_delay; lo and hi are Phi of Eq. shuffle).
-template <int NSUB, int R, bool LAST>
+// Word q of outputs 2v and 2v + 1 into r0, r1.
+template <int NSUB, int R>
+__device__ __forceinline__ void radix2_words(const uint32_t* src, int v, int q, uint32_t& r0,
+                                             uint32_t& r1) {
+  constexpr int PW = tree_pitch(NSUB);
+  const int lo = tree_phi(R, 2 * v), hi = tree_phi(R, 2 * v + 1);
+  const int sft = tree_theta(R, 2 * v);  // output 2v + 1: sft + 1
+  const uint32_t a = src[lo * PW + q];
+  const uint32_t* h = src + hi * PW + q + (sft >> 1);
+  const int ps = (sft & 1) * 16;
+  const uint32_t h0 = __funnelshift_r(h[0], h[1], ps), h1 = __funnelshift_r(h[1], h[2], ps);
+  r0 = a + h0;
+  r1 = a + half_shift(h0, h1);
+}
+
+template <int NSUB, int R, bool LAST, bool OUT8>
 __device__ __forceinline__ void tree_radix2(const uint32_t* src, uint32_t* dst, const TreeOut& o) {
   constexpr int T = tree_tile(NSUB), WW = tree_words(NSUB), PW = tree_pitch(NSUB);
-  constexpr int QN = LAST ? T / 2 : WW;
-  for (int e = threadIdx.x; e < (NSUB / 2) * QN; e += kTreeThreads) {
-    const int v = e / QN;
-    const int q = e - v * QN;
-    const int o0 = 2 * v;
-    if (LAST && o0 >= o.nrow) continue;
-    const int lo = tree_phi(R, 2 * v), hi = tree_phi(R, 2 * v + 1);
-    const int sft = tree_theta(R, 2 * v);  // output 2v + 1: sft + 1
-    const uint32_t a = src[lo * PW + q];
-    const uint32_t* h = src + hi * PW + q + (sft >> 1);
-    const int ps = (sft & 1) * 16;
-    const uint32_t h0 = __funnelshift_r(h[0], h[1], ps), h1 = __funnelshift_r(h[1], h[2], ps);
-    const uint32_t r0 = a + h0, r1 = a + half_shift(h0, h1);
-    if (LAST) {
-      o.S[(int64_t)(o.r0 + o0) * o.s_pitch + q] = r0;
-      if (o0 + 1 < o.nrow) o.S[(int64_t)(o.r0 + o0 + 1) * o.s_pitch + q] = r1;
-    } else {
-      dst[o0 * PW + q] = r0;
-      dst[(o0 + 1) * PW + q] = r1;
+  if constexpr (LAST && OUT8) {
+    constexpr int QN = T / 4;
+    for (int e = threadIdx.x; e < (NSUB / 2) * QN; e += kTreeThreads) {
+      const int v = e / QN;
+      const int q = e - v * QN;
+      const int o0 = 2 * v;
+      if (o0 >= o.nrow) continue;
+      uint32_t a0, a1, b0, b1;
+      radix2_words<NSUB, R>(src, v, 2 * q, a0, a1);
+      radix2_words<NSUB, R>(src, v, 2 * q + 1, b0, b1);
+      o.S[(int64_t)(o.r0 + o0) * o.s_pitch + q] = pack_bytes(a0, b0);
+      if (o0 + 1 < o.nrow) o.S[(int64_t)(o.r0 + o0 + 1) * o.s_pitch + q] = pack_bytes(a1, b1);
+    }
+  } else {
+    constexpr int QN = LAST ? T / 2 : WW;
+    for (int e = threadIdx.x; e < (NSUB / 2) * QN; e += kTreeThreads) {
+      const int v = e / QN;
+      const int q = e - v * QN;
+      const int o0 = 2 * v;
+      if (LAST && o0 >= o.nrow) continue;
+      uint32_t r0, r1;
+      radix2_words<NSUB, R>(src, v, q, r0, r1);
+      if (LAST) {
+        o.S[(int64_t)(o.r0 + o0) * o.s_pitch + q] = r0;
+        if (o0 + 1 < o.nrow) o.S[(int64_t)(o.r0 + o0 + 1) * o.s_pitch + q] = r1;
+      } else {
+        dst[o0 * PW + q] = r0;
+        dst[(o0 + 1) * PW + q] = r1;
+      }
     }
   }
 }
 
 // Steps I .. log2 N' - 1, reading src and writing dst (buffers alternate).
-template <int NSUB, int I>
+template <int NSUB, int I, bool OUT8>
 __device__ __forceinline__ void tree_passes(uint32_t* src, uint32_t* dst, const TreeOut& o) {
   constexpr int M = (NSUB >= 2) + (NSUB >= 4) + (NSUB >= 8) + (NSUB >= 16) + (NSUB >= 32) +
                     (NSUB >= 64) + (NSUB >= 128);  // log2 N'
   if constexpr (I + 1 < M) {
-    tree_radix4<NSUB, (1 << I), I + 2 == M>(src, dst, o);
+    tree_radix4<NSUB, (1 << I), I + 2 == M, OUT8>(src, dst, o);
     if constexpr (I + 2 < M) {
       __syncthreads();
-      tree_passes<NSUB, I + 2>(dst, src, o);
+      tree_passes<NSUB, I + 2, OUT8>(dst, src, o);
     }
   } else if constexpr (I < M) {
-    tree_radix2<NSUB, (1 << I), true>(src, dst, o);
+    tree_radix2<NSUB, (1 << I), true, OUT8>(src, dst, o);
   }
 }
 
-template <int NSUB>
+template <int NSUB, bool OUT8>
 __global__ void __launch_bounds__(kTreeThreads) k_tree_stage1(const TreeS1 p) {
   constexpr int T = tree_tile(NSUB);
   constexpr int WW = tree_words(NSUB);
@@ -236,13 +295,13 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_stage1(const TreeS1 p) {
   TreeOut o;
   o.r0 = __ldg(p.roff + n);
   o.nrow = __ldg(p.roff + n + 1) - o.r0;
-  o.S = p.S + t0 / 2;
+  o.S = p.S + t0 / (OUT8 ? 4 : 2);
   o.s_pitch = p.s_pitch;
-  tree_passes<NSUB, 0>(buf0, buf1, o);
+  tree_passes<NSUB, 0, OUT8>(buf0, buf1, o);
 }
 
 struct TreeS2 {
-  const uint32_t* S;      // stage-1 rows, two 16-bit samples per word
+  const uint32_t* S;      // stage-1 rows: two 16-bit (or four 8-bit) samples a word
   int64_t s_pitch;        // words per S row
   const int2* tab;        // [trial][sub-band] {S row, shift}
   int nsb, ndm;
@@ -376,27 +435,132 @@ __global__ void __launch_bounds__(kS2Warps * 32, 5) k_tree_stage2(const TreeS2 p
   }
 }
 
-template <int NSUB>
+// Stage 2 over 8-bit trails (four samples a word): the same per-trial sum
+// over sub-bands, half the loads.  A lane's words are shifted by the trial's
+// sample offset mod 4 (one byte a sample) with the next word taken from the
+// neighbouring lane, as above; then two sub-bands are added in each byte
+// lane (their sums below 128 each, so no carry) and the pair is spread into
+// 16-bit sums, samples {0, 2} by a mask and {1, 3} by a byte permute.  The
+// host takes this kernel only where a trial's total fits 16 bits.
+constexpr int kS2W8 = kS2Tile / 128;  // words per lane (four samples each, stride 32 words)
+
+__global__ void __launch_bounds__(kS2Warps * 32, 5) k_tree_stage2_b8(const TreeS2 p) {
+  extern __shared__ int2 s_tab[];
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int ntb = (p.ndm + kS2Warps - 1) / kS2Warps;
+  const int d0 = (int)(blockIdx.x % ntb) * kS2Warps;
+  const int64_t t0 = (int64_t)(blockIdx.x / ntb) * kS2Tile;
+  const int nd = min(kS2Warps, p.ndm - d0);
+  for (int e = threadIdx.x; e < nd * p.nsb; e += blockDim.x)
+    s_tab[e] = p.tab[(int64_t)d0 * p.nsb + e];
+  __syncthreads();
+  if (warp >= nd) return;
+  const int d = d0 + warp;
+  const int2* tab = s_tab + warp * p.nsb;
+  uint32_t ev[kS2W8], od[kS2W8];
+#pragma unroll
+  for (int j = 0; j < kS2W8; ++j) ev[j] = od[j] = 0u;
+
+  // words of sub-band n (and lane 0's word after them); returns the shift
+  auto fetch = [&](int n, uint32_t (&w)[kS2W8], uint32_t& tail) -> int {
+    const int2 rs = tab[n];
+    const int64_t e0 = t0 + rs.y;
+    const uint32_t* src = p.S + (int64_t)rs.x * p.s_pitch + (e0 >> 2) + lane;
+#pragma unroll
+    for (int j = 0; j < kS2W8; ++j) w[j] = __ldg(src + 32 * j);
+    tail = lane == 0 ? __ldg(src + 32 * kS2W8) : 0u;
+    return (int)(e0 & 3);
+  };
+  // in place: word j of the lane moved on by r samples (r is the trial's,
+  // the same for the whole warp)
+  auto shift = [&](uint32_t (&w)[kS2W8], uint32_t tail, int r) {
+    if (r == 0) return;
+#pragma unroll
+    for (int j = 0; j < kS2W8; ++j) {
+      const uint32_t give = lane == 0 ? (j + 1 < kS2W8 ? w[(j + 1) % kS2W8] : tail) : w[j];
+      const uint32_t nx = __shfl_sync(0xffffffffu, give, (lane + 1) & 31);
+      w[j] = __funnelshift_r(w[j], nx, 8 * r);
+    }
+  };
+  auto spread = [&](int j, uint32_t a) {
+    ev[j] += a & 0x00FF00FFu;
+    od[j] += __byte_perm(a, 0u, 0x4341u);
+  };
+
+  // sub-bands n and n + 1 summed from one pair of buffers while the loads of
+  // n + 2 and n + 3 are in flight in the other (eight words a lane in
+  // flight, as many as the 16-bit kernel's one sub-band ahead)
+  auto sum_pair = [&](uint32_t (&x)[kS2W8], uint32_t tx, int rx, uint32_t (&y)[kS2W8],
+                      uint32_t ty, int ry, bool two) {
+    shift(x, tx, rx);
+    if (two) {
+      shift(y, ty, ry);
+#pragma unroll
+      for (int j = 0; j < kS2W8; ++j) spread(j, x[j] + y[j]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kS2W8; ++j) spread(j, x[j]);
+    }
+  };
+  uint32_t a0[kS2W8], a1[kS2W8], b0[kS2W8], b1[kS2W8];
+  uint32_t ta0 = 0u, ta1 = 0u, tb0 = 0u, tb1 = 0u;
+  int ra0 = fetch(0, a0, ta0), ra1 = 0, rb0 = 0, rb1 = 0;
+  if (p.nsb > 1) ra1 = fetch(1, a1, ta1);
+  for (int n = 0;;) {
+    if (n + 2 < p.nsb) rb0 = fetch(n + 2, b0, tb0);
+    if (n + 3 < p.nsb) rb1 = fetch(n + 3, b1, tb1);
+    sum_pair(a0, ta0, ra0, a1, ta1, ra1, n + 1 < p.nsb);
+    if ((n += 2) >= p.nsb) break;
+    if (n + 2 < p.nsb) ra0 = fetch(n + 2, a0, ta0);
+    if (n + 3 < p.nsb) ra1 = fetch(n + 3, a1, ta1);
+    sum_pair(b0, tb0, rb0, b1, tb1, rb1, n + 1 < p.nsb);
+    if ((n += 2) >= p.nsb) break;
+  }
+  uint32_t* o = p.out + (int64_t)d * p.out_stride;
+#pragma unroll
+  for (int j = 0; j < kS2W8; ++j) {
+    const uint32_t v[4] = {ev[j] & 0xFFFFu, od[j] & 0xFFFFu, ev[j] >> 16, od[j] >> 16};
+    const int64_t t = t0 + 4 * (lane + 32 * j);
+    if (p.vec_out && t + 4 <= p.nsamps) {
+      *reinterpret_cast<uint2*>(o + t) = make_uint2(v[0], v[1]);
+      *reinterpret_cast<uint2*>(o + t + 2) = make_uint2(v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (t + e < p.nsamps) o[t + e] = v[e];
+    }
+  }
+}
+
+template <int NSUB, bool OUT8>
 cudaError_t launch_stage1(const TreeS1& a, int64_t tiles, int nsb, cudaStream_t st) {
   const size_t smem = 2u * NSUB * tree_pitch(NSUB) * 4u;
-  auto k = k_tree_stage1<NSUB>;
+  auto k = k_tree_stage1<NSUB, OUT8>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<(unsigned)(tiles * nsb), kTreeThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t stage1(int nsub, const TreeS1& a, int64_t tiles, int nsb, cudaStream_t st) {
+// out8: 8-bit trails, compiled for N' <= 64 (N' * max sample < 128 needs
+// N' < 128 even for 1-bit input)
+cudaError_t stage1(int nsub, bool out8, const TreeS1& a, int64_t tiles, int nsb,
+                   cudaStream_t st) {
+#define DD_TREE_CASE(N) \
+  case N:               \
+    return out8 ? launch_stage1<N, true>(a, tiles, nsb, st) : launch_stage1<N, false>(a, tiles, nsb, st);
   switch (nsub) {
-    case 2: return launch_stage1<2>(a, tiles, nsb, st);
-    case 4: return launch_stage1<4>(a, tiles, nsb, st);
-    case 8: return launch_stage1<8>(a, tiles, nsb, st);
-    case 16: return launch_stage1<16>(a, tiles, nsb, st);
-    case 32: return launch_stage1<32>(a, tiles, nsb, st);
-    case 64: return launch_stage1<64>(a, tiles, nsb, st);
-    case 128: return launch_stage1<128>(a, tiles, nsb, st);
+    DD_TREE_CASE(2)
+    DD_TREE_CASE(4)
+    DD_TREE_CASE(8)
+    DD_TREE_CASE(16)
+    DD_TREE_CASE(32)
+    DD_TREE_CASE(64)
+    case 128: return out8 ? cudaErrorInvalidValue : launch_stage1<128, false>(a, tiles, nsb, st);
     default: return cudaErrorInvalidValue;
   }
+#undef DD_TREE_CASE
 }
 
 }  // namespace
@@ -469,7 +633,12 @@ dd_status exec_tree(Plan& p, const ExecArgs& a) {
   // S rows: every stage-1 tile writes T samples; stage 2 reads up to len1
   const int64_t pitch = ((tiles * T + 63) / 64) * 64;    // samples
   const int rows = p.tree_roff[nsb];
-  if ((e = p.d_tree_S.ensure(((size_t)rows * pitch / 2 + kS2SlackWords) * 4)) != cudaSuccess)
+  // 8-bit trails where a sub-band's sums stay below 128 and a trial's total
+  // below 2^16 (1- and 2-bit input), else 16-bit
+  const int64_t vmax = (1 << a.in_nbits) - 1;
+  const bool b8 = a.in_nbits <= 2 && Np <= 64 && Np * vmax <= 127 && C * vmax <= 65535;
+  const int spw = b8 ? 4 : 2;
+  if ((e = p.d_tree_S.ensure(((size_t)rows * pitch / spw + kS2SlackWords) * 4)) != cudaSuccess)
     return cuda_status(e);
   TreeS1 s1;
   s1.in = static_cast<const uint8_t*>(a.in);
@@ -477,17 +646,17 @@ dd_status exec_tree(Plan& p, const ExecArgs& a) {
   s1.in_rows = a.in_rows;
   s1.mask = static_cast<const uint8_t*>(p.d_mask.p);
   s1.S = static_cast<uint32_t*>(p.d_tree_S.p);
-  s1.s_pitch = pitch / 2;
+  s1.s_pitch = pitch / spw;
   s1.roff = static_cast<const int32_t*>(p.d_tree_roff.p);
   s1.nbits = a.in_nbits;
   s1.nsb = nsb;
   {
     KernelTimer kt(&p, DD_KERNEL_DEDISP, a.st);
-    if ((e = stage1(Np, s1, tiles, nsb, a.st)) != cudaSuccess) return cuda_status(e);
+    if ((e = stage1(Np, b8, s1, tiles, nsb, a.st)) != cudaSuccess) return cuda_status(e);
   }
   TreeS2 s2;
   s2.S = static_cast<const uint32_t*>(p.d_tree_S.p);
-  s2.s_pitch = pitch / 2;
+  s2.s_pitch = pitch / spw;
   s2.tab = static_cast<const int2*>(p.d_tree_tab.p);
   s2.nsb = nsb;
   s2.ndm = n;
@@ -501,7 +670,9 @@ dd_status exec_tree(Plan& p, const ExecArgs& a) {
   const unsigned grid = (unsigned)(t2 * ((n + kS2Warps - 1) / kS2Warps));
   const size_t smem = (size_t)kS2Warps * nsb * sizeof(int2);
   KernelTimer kt(&p, DD_KERNEL_STAGE2, a.st);
-  if (s2.flush < nsb)
+  if (b8)
+    k_tree_stage2_b8<<<grid, kS2Warps * 32, smem, a.st>>>(s2);
+  else if (s2.flush < nsb)
     k_tree_stage2<true><<<grid, kS2Warps * 32, smem, a.st>>>(s2);
   else
     k_tree_stage2<false><<<grid, kS2Warps * 32, smem, a.st>>>(s2);

@@ -156,3 +156,22 @@ def test_tree_many_tiles_bit_exact(orc, nsub, nbits):
     got = _run_tree(plan, x, nbits, nsamps)
     ref = orc.tree_piecewise(x, nbits, 1024, nsub, nsamps, _ext(orc, plan), mask)
     assert np.array_equal(got, ref), np.argwhere(got != ref)[:5]
+
+
+@pytest.mark.parametrize("nsub,nbits", [(32, 2), (64, 1), (128, 1), (64, 2)])
+def test_tree_saturated_trails_bit_exact(orc, nsub, nbits):
+    """Runs of saturated input rows beside uniform noise: the trails reach
+    N' * (2^nbits - 1).  96 and 64 (2-bit x 32, 1-bit x 64) are kept in
+    8-bit lanes, four samples a word, and stage 2 adds two sub-bands in each
+    byte lane; 128 and 192 take 16-bit lanes.  Every trial below the
+    diagonal, full rows, a ragged gulp."""
+    torch_cuda()
+    plan = _survey_tree_plan(orc, nsub)
+    nsamps = 6151
+    rows = plan.input_rows(nsamps, tree=True)
+    x = synth.uniform_packed(230 + nsub + nbits, nbits, rows, 1024, nbits)
+    x[(np.arange(rows) // 400) % 2 == 1] = 0xFF
+    got = _run_tree(plan, x, nbits, nsamps)
+    ref = orc.tree_piecewise(x, nbits, 1024, nsub, nsamps, _ext(orc, plan))
+    assert ref.max() == 1024 * ((1 << nbits) - 1)
+    assert np.array_equal(got, ref), np.argwhere(got != ref)[:5]
