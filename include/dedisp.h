@@ -295,8 +295,11 @@ dd_status dd_execute(dd_plan plan, int64_t nsamps_out, const void *in, int in_nb
  * its tables and kill mask from pageable host memory.
  * Returns DD_ERR_OOM, before launching anything, when the staged image and
  * tables need more than the array (the image takes about nchans *
- * (nsamps_out + max_delay) bytes per staged sample: half a byte for 1- and
- * 2-bit input, 1, 2 or 4 bytes for 4-bit, 8-bit or float input).
+ * (nsamps_out + max_delay) times the bytes per staged sample: half a byte
+ * for 1- and 2-bit input, 1 for 4-bit, 4/3 for 8-bit (three samples a
+ * word), 4 for float input).  The output rows are uint32 (float for float
+ * input): a plan with scaled output (dd_plan_set_output_bits below 32) is
+ * rejected with DD_ERR_INVALID_ARG.
  * All calls share the array and each starts by reloading it: calls whose work
  * overlaps on the GPU (other streams or threads) race, so the caller must
  * serialise them.  Its device-side bound flags are read with
