@@ -165,3 +165,22 @@ def test_subband_multi_tile_items_full_rows(orc, nbits):
     got, _ = run_direct(plan, x, nbits, nsamps, subband=True)
     ref = orc.subband(x, nbits, 1024, 32, 32, odelays(orc, plan), nsamps)
     assert np.array_equal(got, ref), np.argwhere(got != ref)[:5]
+
+
+@pytest.mark.parametrize("nbits", [2, 8])
+def test_subband_host_pointers_with_killmask(orc, nbits):
+    """numpy input and output (the library copies both ways) with a kill
+    mask, on the 8-bit-lane (2-bit input) and 16-bit-lane (8-bit input)
+    intermediates: equal to the oracle over masked input."""
+    plan = _plan(step=7)
+    mask = np.ones(1024, np.uint8)
+    mask[[0, 31, 32, 500, 1023]] = 0
+    plan.set_killmask(mask)
+    nsamps = 2300
+    rows = nsamps + plan.subband_max_delay
+    x = synth.uniform_packed(27 + nbits, nbits, rows, 1024, nbits)
+    out = np.zeros((plan.dm_count, nsamps), np.uint32)
+    plan.execute(x, nbits, nsamps, out, subband=True)
+    assert plan.device_status() == 0
+    ref = orc.subband(x, nbits, 1024, 32, 32, odelays(orc, plan), nsamps, mask=mask)
+    assert np.array_equal(out, ref)
