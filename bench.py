@@ -644,8 +644,10 @@ def run_tree(a, x, G, peak_adds):
         adds1 = c["nchans"] * int(np.log2(nsub)) * len1
         adds2 = len(dms) * (c["nchans"] // nsub) * G
         adds = adds1 + adds2
-        # 2-bit trails of N' channels below 128: the library keeps them in 8-bit lanes
-        b8 = nsub * 3 < 128
+        # 2-bit trails of N' channels below 256: the library keeps them in 8-bit
+        # lanes, and adds two sub-bands a byte lane below 128
+        b8 = nsub * 3 < 256
+        pairs = nsub * 3 < 128
         res["nsub_%d" % nsub] = {
             "dm_limit": lim, "ndm": len(dms), "dm_max": float(dms[-1]),
             "ms_per_step": t_ms, "kernels_ms": t1_ms + t2_ms,
@@ -657,8 +659,9 @@ def run_tree(a, x, G, peak_adds):
                                   "lanes": "16-bit pairs, %d-bit trails out" % (8 if b8 else 16),
                                   "frac_of_int_add_probe": adds1 / (t1_ms / 1e3) / peak_adds},
                        "stage2": {"ms": t2_ms, "adds": adds2,
-                                  "lanes": ("8-bit pairs of sub-bands into 16-bit sums" if b8
-                                            else "16-bit"),
+                                  "lanes": ("8-bit, %s into 16-bit sums"
+                                            % ("pairs of sub-bands" if pairs else "one sub-band")
+                                            if b8 else "16-bit"),
                                   "frac_of_int_add_probe": adds2 / (t2_ms / 1e3) / peak_adds}},
             "app_a_smear_us_at_dm_max": 1e6 * 0.75 * float(dms[-1]) * 4.148808e3 / c["f0"] ** 2
             * (nsub / c["nchans"]) ** 2 * (c["df"] * c["nchans"] / c["f0"]) ** 2

@@ -10,9 +10,9 @@
 // every step there between two buffers, and writes only the trails stage 2
 // reads (d' up to the largest d'_n(d) of the sub-band).  Samples are 16-bit
 // lanes, two per 32-bit word, so one add serves two samples: a sub-band's
-// sums (N' * max sample) stay below 2^16.  Where they stay below 128 (1- and
-// 2-bit input, N' * max sample < 128) the trails are written in 8-bit lanes,
-// four samples a word, and stage 2 reads half the words.
+// sums (N' * max sample) stay below 2^16.  Where they stay below 256 the
+// trails are written in 8-bit lanes, four samples a word, and stage 2 reads
+// half the words.
 //
 // Step i (radix r = 2^i), Eq. (tree_algorithm_first .. last):
 //   A'[2v + j][t] = A[Phi(r, 2v)][t] + A[Phi(r, 2v + 1)][t + Theta(i, 2v + j)]
@@ -438,12 +438,14 @@ __global__ void __launch_bounds__(kS2Warps * 32, 5) k_tree_stage2(const TreeS2 p
 // Stage 2 over 8-bit trails (four samples a word): the same per-trial sum
 // over sub-bands, half the loads.  A lane's words are shifted by the trial's
 // sample offset mod 4 (one byte a sample) with the next word taken from the
-// neighbouring lane, as above; then two sub-bands are added in each byte
-// lane (their sums below 128 each, so no carry) and the pair is spread into
-// 16-bit sums, samples {0, 2} by a mask and {1, 3} by a byte permute.  The
-// host takes this kernel only where a trial's total fits 16 bits.
+// neighbouring lane, as above; then (PAIRS: trails below 128) two sub-bands
+// are added in each byte lane without a carry, or (trails below 256) each
+// sub-band is taken alone, and spread into 16-bit sums, samples {0, 2} by a
+// mask and {1, 3} by a byte permute.  The host takes this kernel only where
+// a trial's total fits 16 bits.
 constexpr int kS2W8 = kS2Tile / 128;  // words per lane (four samples each, stride 32 words)
 
+template <bool PAIRS>
 __global__ void __launch_bounds__(kS2Warps * 32, 5) k_tree_stage2_b8(const TreeS2 p) {
   extern __shared__ int2 s_tab[];
   const int warp = threadIdx.x >> 5;
@@ -497,7 +499,14 @@ __global__ void __launch_bounds__(kS2Warps * 32, 5) k_tree_stage2_b8(const TreeS
     if (two) {
       shift(y, ty, ry);
 #pragma unroll
-      for (int j = 0; j < kS2W8; ++j) spread(j, x[j] + y[j]);
+      for (int j = 0; j < kS2W8; ++j) {
+        if (PAIRS) {
+          spread(j, x[j] + y[j]);
+        } else {
+          spread(j, x[j]);
+          spread(j, y[j]);
+        }
+      }
     } else {
 #pragma unroll
       for (int j = 0; j < kS2W8; ++j) spread(j, x[j]);
@@ -543,8 +552,7 @@ cudaError_t launch_stage1(const TreeS1& a, int64_t tiles, int nsb, cudaStream_t 
   return cudaGetLastError();
 }
 
-// out8: 8-bit trails, compiled for N' <= 64 (N' * max sample < 128 needs
-// N' < 128 even for 1-bit input)
+// out8: 8-bit trails (N' * max sample < 256)
 cudaError_t stage1(int nsub, bool out8, const TreeS1& a, int64_t tiles, int nsb,
                    cudaStream_t st) {
 #define DD_TREE_CASE(N) \
@@ -557,7 +565,7 @@ cudaError_t stage1(int nsub, bool out8, const TreeS1& a, int64_t tiles, int nsb,
     DD_TREE_CASE(16)
     DD_TREE_CASE(32)
     DD_TREE_CASE(64)
-    case 128: return out8 ? cudaErrorInvalidValue : launch_stage1<128, false>(a, tiles, nsb, st);
+    DD_TREE_CASE(128)
     default: return cudaErrorInvalidValue;
   }
 #undef DD_TREE_CASE
@@ -633,10 +641,12 @@ dd_status exec_tree(Plan& p, const ExecArgs& a) {
   // S rows: every stage-1 tile writes T samples; stage 2 reads up to len1
   const int64_t pitch = ((tiles * T + 63) / 64) * 64;    // samples
   const int rows = p.tree_roff[nsb];
-  // 8-bit trails where a sub-band's sums stay below 128 and a trial's total
-  // below 2^16 (1- and 2-bit input), else 16-bit
+  // 8-bit trails where a sub-band's sums stay below 256 and a trial's total
+  // below 2^16, added two sub-bands a byte lane where they stay below 128;
+  // else 16-bit
   const int64_t vmax = (1 << a.in_nbits) - 1;
-  const bool b8 = a.in_nbits <= 2 && Np <= 64 && Np * vmax <= 127 && C * vmax <= 65535;
+  const bool b8 = Np * vmax <= 255 && C * vmax <= 65535;
+  const bool pairs = Np * vmax <= 127;
   const int spw = b8 ? 4 : 2;
   if ((e = p.d_tree_S.ensure(((size_t)rows * pitch / spw + kS2SlackWords) * 4)) != cudaSuccess)
     return cuda_status(e);
@@ -670,8 +680,10 @@ dd_status exec_tree(Plan& p, const ExecArgs& a) {
   const unsigned grid = (unsigned)(t2 * ((n + kS2Warps - 1) / kS2Warps));
   const size_t smem = (size_t)kS2Warps * nsb * sizeof(int2);
   KernelTimer kt(&p, DD_KERNEL_STAGE2, a.st);
-  if (b8)
-    k_tree_stage2_b8<<<grid, kS2Warps * 32, smem, a.st>>>(s2);
+  if (b8 && pairs)
+    k_tree_stage2_b8<true><<<grid, kS2Warps * 32, smem, a.st>>>(s2);
+  else if (b8)
+    k_tree_stage2_b8<false><<<grid, kS2Warps * 32, smem, a.st>>>(s2);
   else if (s2.flush < nsb)
     k_tree_stage2<true><<<grid, kS2Warps * 32, smem, a.st>>>(s2);
   else

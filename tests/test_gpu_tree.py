@@ -158,13 +158,14 @@ def test_tree_many_tiles_bit_exact(orc, nsub, nbits):
     assert np.array_equal(got, ref), np.argwhere(got != ref)[:5]
 
 
-@pytest.mark.parametrize("nsub,nbits", [(32, 2), (64, 1), (128, 1), (64, 2)])
+@pytest.mark.parametrize("nsub,nbits", [(32, 2), (64, 1), (128, 1), (64, 2), (16, 4), (32, 4)])
 def test_tree_saturated_trails_bit_exact(orc, nsub, nbits):
     """Runs of saturated input rows beside uniform noise: the trails reach
-    N' * (2^nbits - 1).  96 and 64 (2-bit x 32, 1-bit x 64) are kept in
-    8-bit lanes, four samples a word, and stage 2 adds two sub-bands in each
-    byte lane; 128 and 192 take 16-bit lanes.  Every trial below the
-    diagonal, full rows, a ragged gulp."""
+    N' * (2^nbits - 1).  All but the last are kept in 8-bit lanes, four
+    samples a word: 96 and 64 (2-bit x 32, 1-bit x 64), where stage 2 adds
+    two sub-bands in each byte lane, and 128, 192 and 240 (1-bit x 128,
+    2-bit x 64, 4-bit x 16), one sub-band at a time; 480 (4-bit x 32) takes
+    16-bit lanes.  Every trial below the diagonal, full rows, a ragged gulp."""
     torch_cuda()
     plan = _survey_tree_plan(orc, nsub)
     nsamps = 6151
