@@ -800,12 +800,14 @@ static dd_status exec_subband(Plan& p, const ExecArgs& a, int fmt) {
   // intermediate: 8-bit image rows when stage-1 sums stay below 128 (1- and
   // 2-bit input; stage 2 then adds two sub-bands a lane and a trial's total
   // fits 16 bits), else 16-bit rows when they fit, else 32-bit.  The 8-bit
-  // stages are compiled for the default tiles only (stage 1: 32 trials, 4
-  // words a lane; stage 2: 32 trials, 8 words a lane).
+  // stages exist as multi-tile kernels of the default tiles only (stage 1:
+  // 32 trials, 4 words a lane; stage 2: 32 trials, 8 words a lane) and for
+  // uint32 output rows.
   const int64_t vmax1 = (int64_t)Np * vmax_in;
-  const bool byte = fmt == FMT_NIB && vmax1 <= 127 && (int64_t)C * vmax_in <= 65535 &&
-                    p.out_bits == 32 && tile_cfg_index(t1) == 0 &&
-                    tile_cfg_index(tuning_for(p.tune, FMT_SB8)) == 4;
+  const bool byte =
+      fmt == FMT_NIB && vmax1 <= 127 && (int64_t)C * vmax_in <= 65535 && p.out_bits == 32 &&
+      multi_tile_compiled(FMT_NIB, OUT_BYTEIMG, false, tile_cfg_index(t1)) &&
+      multi_tile_compiled(FMT_SB8, OUT_U32, false, tile_cfg_index(tuning_for(p.tune, FMT_SB8)));
   const bool half = !byte && vmax1 <= 65535;
   const int fmt2 = byte ? FMT_SB8 : (half ? FMT_HALF : FMT_U32);
   const int bi = b_index(B);
